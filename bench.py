@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the LJ short-range force path on GB300.
+
+Workload (one "step" = one velocity-Verlet MD step: half kick + drift, cell
+rebinning or Verlet-list rebuild when due, one force evaluation, half kick):
+homogeneous LJ fluid, 1,048,576 particles at density 0.75 in a periodic cube
+(L = 111.82), cutoff 2.5, Verlet skin 0.3 rebuilt every 10 steps,
+Maxwell-Boltzmann velocities at T = 1.0, dt = 0.002; FP32 pair arithmetic with
+FP64 accumulation.  The configuration (container x interaction order x
+Newton-3) is picked by the library's full-search tuner before timing.
+
+Metric: unique in-cutoff pair evaluations per second (a pair counts once per
+force evaluation whatever the Newton-3 setting), whole job over all ranks.
+Timing: per-step CUDA events on the library's stream; the L2 is flushed
+(256 MiB write) between timed steps, outside the events.
+
+`--impl reference` times the FP64 CPU oracle (linked-cell mode, all host
+cores) on the same workload instead: each step is one full force evaluation.
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(the force path of one box does not shard without a halo exchange, which is
+not built); no data-path collective, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FLOPS_PER_PAIR = {0: 23, 1: 26, 2: 26}   # useful flops per unique pair by Newton-3 mode
+WORKLOAD = ("homogeneous LJ fluid, 1,048,576 particles, density 0.75 (L=111.82), rc 2.5, skin 0.3 "
+            "(Verlet rebuild every 10 steps), T=1.0 Maxwell-Boltzmann, velocity Verlet dt=0.002, "
+            "FP32 pair math with FP64 accumulation")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1048576)
+    ap.add_argument("--tune", default="full", choices=["full", "fixed"])
+    ap.add_argument("--cfg", default=None, help="fixed configuration, e.g. 1,5,0,1 (container,order,param,n3)")
+    ap.add_argument("--samples", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--out", default=None, help="also append the JSON line to this file")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def traffic_from_profiles(cfg_name):
+    """DRAM bytes per force-kernel launch from the committed ncu summary, if it
+    was taken for this configuration (line: 'traffic <config> <bytes>')."""
+    path = os.path.join(ROOT, "profiles", "force_c2_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and parts[0] == "traffic" and parts[1] == cfg_name:
+            return float(parts[2])
+    return None
+
+
+def cpu_oracle_rate(system, evals_max=3, budget_s=25.0):
+    """The FP64 oracle's linked-cell force evaluation on the host cores."""
+    import oracle
+    oracle.build()
+    t_total, pairs_total, k = 0.0, 0, 0
+    while k < evals_max and t_total < budget_s:
+        t0 = time.perf_counter()
+        _, _, _, npairs = oracle.forces_cells(system.pos, system.L, system.rc)
+        t_total += time.perf_counter() - t0
+        pairs_total += npairs
+        k += 1
+    return pairs_total / t_total, oracle.num_threads(), k, t_total
+
+
+def run_reference(args, ws, rank, pg):
+    from paper_2512_03565_gb300 import workloads as W
+    if rank != 0:
+        return 0
+    s = W.config2(args.n)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(s, evals_max=1)
+    times, pairs = [], []
+    import oracle
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, _, _, npairs = oracle.forces_cells(s.pos, s.L, s.rc)
+        times.append(time.perf_counter() - t0)
+        pairs.append(npairs)
+    value = float(np.sum(pairs) / np.sum(times))
+    line = {
+        "impl": "reference", "metric": "LJ in-cutoff pair evals/s", "value": value, "unit": "pairs/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; reference step = one FP64 linked-cell force evaluation (no time step)",
+                   "n": s.n},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} full linked-cell force evaluations of the {s.n}-particle system"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local, pg):
+    import torch
+    from paper_2512_03565_gb300 import build as B
+    from paper_2512_03565_gb300 import ljgb as lj
+    from paper_2512_03565_gb300 import workloads as W
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # replica per rank: same workload shape, rank-specific seed
+    s = W.homogeneous(args.n, 0.75, W.BASE_SEED + 1 + 7919 * rank, T=1.0, rc=2.5, skin=0.3)
+    pos_d = torch.from_numpy(s.pos.view(np.int32)).to(dev)
+    vel_d = torch.from_numpy(s.vel).to(dev)
+    d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP32_ACC64, stream=stream)
+    d.set_particles(pos_d, vel_d)
+
+    # configuration: full search (Sec. 2.3.2) over every valid configuration
+    times = {}
+    if args.tune == "full":
+        cfg, times = d.tune(0, args.samples)
+    else:
+        cfg = lj.config(*[int(v) for v in (args.cfg or "1,5,0,1").split(",")])
+    cfg_name = lj.config_name(cfg)
+    timed = {k: v for k, v in times.items() if not math.isnan(v)}
+    best_fixed = min(timed.items(), key=lambda kv: kv[1]) if timed else (cfg_name, None)
+
+    dt, rebuild = 0.002, 10
+    for _ in range(args.warmup):
+        d.integrate(dt, 1, cfg, rebuild_every=rebuild)
+    torch.cuda.synchronize(dev)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    _, _, launches0 = d.timing(1)
+    pairs = []
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        d.integrate(dt, 1, cfg, rebuild_every=rebuild)
+        ev[k][1].record(stream)
+        pairs.append(int(d.counters()[1]))
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    force_ms, force_n, launches1 = d.timing(0)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    my_pairs = float(sum(pairs))
+    if pg:
+        t = torch.tensor([total_s, my_pairs], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        tsum = t.clone()
+        pg.all_reduce(tsum, op=pg.ReduceOp.SUM)
+        total_s_all, pairs_all = float(tmax[0]), float(tsum[1])
+    else:
+        total_s_all, pairs_all = total_s, my_pairs
+    value = pairs_all / total_s_all
+
+    # roofline of the dominant kernel (the force kernel): useful FP32 flops of
+    # the unique in-cutoff pairs per launch / mean launch duration
+    avg_force_s = (force_ms / max(force_n, 1)) / 1e3
+    flops_launch = FLOPS_PER_PAIR[cfg.newton3] * float(np.mean(pairs))
+    achieved = flops_launch / avg_force_s / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic_from_profiles(cfg_name), "kernel_ms": avg_force_s * 1e3,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FFMA)",
+            "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3]}
+
+    # end to end through the public API with host buffers: positions (doubles)
+    # from pinned host memory in, one force evaluation, forces back to host
+    e2e = None
+    if not args.no_e2e:
+        x_host = torch.from_numpy((s.pos.astype(np.float64) + 0.5) * (s.L / 2.0 ** 32)).pin_memory()
+        f_host = torch.empty((3, s.n), dtype=torch.float64).pin_memory()
+        lib = lj.load()
+        k_e2e = max(3, min(args.steps, 10))
+        for it in range(k_e2e + 2):
+            if it == 2:
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+            st = lib.lj_set_particles(d.h, s.n, x_host.data_ptr(), None, 1.0, 0)
+            st = st or lib.lj_compute_forces(d.h, cfg, None, None)
+            st = st or lib.lj_get_forces(d.h, f_host.data_ptr(), 0)
+            if st:
+                raise lj.LJError(st, lib.lj_last_error(d.h).decode())
+        t_e2e = (time.perf_counter() - t0) / k_e2e
+        np_e2e = int(d.counters()[1])
+        e2e = {"value": np_e2e / t_e2e * ws, "unit": "pairs/s", "h2d_bytes_per_step": 3 * s.n * 8,
+               "d2h_bytes_per_step": 3 * s.n * 8, "ms_per_step": t_e2e * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, cores, k, tsec = cpu_oracle_rate(s)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{k} FP64 linked-cell force evaluation(s) of the {s.n}-particle system ({tsec:.1f} s)"}
+
+    line = {
+        "metric": "LJ in-cutoff pair evals/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": s.n, "config": cfg_name, "tuner": args.tune,
+                   "cfg_tuple": [cfg.container, cfg.order, cfg.param, cfg.newton3],
+                   "best_fixed": best_fixed[0], "best_fixed_ms": best_fixed[1],
+                   "tuned_force_ms": times.get(cfg_name), "pairs_per_step": float(np.mean(pairs)),
+                   "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{ws}",
+                   "wall_s": t_wall, "tuning_times_ms": timed},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clk,
+    }
+    if rank == 0:
+        out = json.dumps(line)
+        print(out, flush=True)
+        if args.out:
+            with open(args.out, "a") as f:
+                f.write(out + "\n")
+    d.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, ws, rank, pg)
+        if pg:
+            pg.destroy_process_group()
+        return rc
+    return run_ours(args, ws, rank, local, pg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,258 @@
+/*
+ * ljgb.h -- C ABI of the GB300 (sm_103a) Lennard-Jones short-range force library.
+ *
+ * The library computes the hot path of "Tuning of Vectorization Parameters
+ * for Molecular Dynamics Simulations in AutoPas" (arXiv 2512.03565):
+ *   - the pairwise force sum F_i = sum_j F_ij (Sec. 2.1, Eq. 1) over pairs
+ *     within the cutoff (Sec. 2.1), Lennard-Jones 12-6 (named in Sec. 4.1;
+ *     textbook form U = 4 eps [(sigma/r)^12 - (sigma/r)^6], truncated);
+ *   - neighbour identification by Linked Cells and by Verlet lists with a skin
+ *     (Sec. 2.1.1);
+ *   - the interaction order, i.e. which particles of the two lists a functor
+ *     holds against which (Sec. 4.1, Fig. 4: 1/V, V/1, 2/V2, V2/2), as GPU
+ *     orders chosen at run time; Newton's third law on or off (Sec. 4.1.3);
+ *   - the full-search auto-tuner over the Cartesian product of configurations
+ *     (Sec. 2.3.2) and a learned tuner (the data-driven tuning of Sec. 6);
+ *   - velocity-Verlet time integration (Sec. 2.1).
+ *
+ * Conventions for every entry point:
+ *   - Status codes only: nothing throws, exits or aborts across the ABI.
+ *     LJ_ERR_* codes are listed below; lj_last_error() gives a message.
+ *   - Geometry: a cubic periodic box of edge L.  Positions are stored as 32-bit
+ *     fixed point per axis, x = x_fp * u with u = L / 2^32; the minimum image of
+ *     a difference is the wrapping 32-bit difference read as signed.  A pair
+ *     interacts iff 0 < R^2 <= floor((r_c/u)^2), R^2 the exact integer sum of
+ *     squared fixed-point differences (pairs at zero separation are excluded).
+ *   - Arrays are SoA with 3*n entries: x[0..n), y[0..n), z[0..n).  Arrays
+ *     passed in are borrowed for the duration of the call only.
+ *     on_device = 1 means a CUDA device pointer (e.g. a torch tensor's
+ *     data_ptr()), 0 a host pointer (pinned or pageable).
+ *   - Ownership: the library owns all of its device state; lj_destroy frees it.
+ *   - Streams: all work is issued on the stream given at lj_init_domain (NULL =
+ *     the legacy default stream).  Calls that return host values synchronise
+ *     that stream.
+ *   - Ordering: forces, positions and velocities are returned in the caller's
+ *     original particle order.
+ *   - Units: reduced LJ units (eps, sigma, mass as given).
+ *   - Threading: one context must not be used from two host threads at once.
+ */
+#ifndef LJGB_H
+#define LJGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lj_ctx lj_ctx;
+
+typedef enum {
+  LJ_OK = 0,
+  LJ_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad config) */
+  LJ_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  LJ_ERR_CAPACITY = 3,   /* a Verlet list overflowed its capacity (the library regrows and rebuilds) */
+  LJ_ERR_SKIN = 4,       /* a particle moved more than skin/2 since the last list build */
+  LJ_ERR_NONFINITE = 5,  /* a force, energy or virial was NaN or infinite */
+  LJ_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+  LJ_ERR_STATE = 7,      /* call out of order (e.g. forces before particles) */
+  LJ_ERR_OOM = 8         /* device allocation failed */
+} lj_status;
+
+typedef enum { LJ_PREC_FP64 = 0, LJ_PREC_FP32_ACC64 = 1 } lj_precision;
+
+/* Neighbour identification (Sec. 2.1.1): linked cells of edge >= r_c, rebinned
+ * at every force evaluation; Verlet lists built on cells of edge >= r_c + skin. */
+typedef enum { LJ_LC = 0, LJ_VL = 1 } lj_container;
+
+/* Interaction orders: the GPU analogues of the paper's register-filling
+ * patterns (Sec. 4.1.1, Fig. 4).
+ *   LJ_ORD_IPT_SMEM  one i per lane, the j tile staged in shared memory and
+ *                    broadcast to the warp (V/1: V i's against one j).
+ *   LJ_ORD_IPT_TMA   as IPT_SMEM, the j tile brought in by bulk asynchronous
+ *                    copies (cp.async.bulk) on an mbarrier double buffer.
+ *   LJ_ORD_KI        k i's per lane (param = k in {2,4}): one j load serves k pairs.
+ *   LJ_ORD_JSPLIT    w lanes per i striding over the j list, shuffle reduction
+ *                    of the i force (param = w in {32,16,8,4,2}): 1/V for
+ *                    w=32, 2/V2 for w=16, V2/2 for w=2.
+ *   LJ_ORD_ROT32     one i and one j per lane, j rotated through the warp by
+ *                    shuffles: a full 32 x 32 tile (the "full/rotated" order).
+ *   LJ_ORD_VL_IPT    Verlet lists only: one i per lane, gathering its list. */
+typedef enum {
+  LJ_ORD_IPT_SMEM = 0,
+  LJ_ORD_IPT_TMA = 1,
+  LJ_ORD_KI = 2,
+  LJ_ORD_JSPLIT = 3,
+  LJ_ORD_ROT32 = 4,
+  LJ_ORD_VL_IPT = 5
+} lj_order;
+
+/* Newton's third law (Sec. 2.1, Sec. 4.1.3): off (every pair evaluated from
+ * both sides), on with the j contribution scattered by FP64 atomics, or on with
+ * a deterministic two-pass reduction (j partials written to a buffer, then
+ * gathered per particle in a fixed order; ROT32 on linked cells only). */
+typedef enum { LJ_N3_OFF = 0, LJ_N3_ATOMIC = 1, LJ_N3_TWOPASS = 2 } lj_newton3;
+
+typedef struct {
+  int32_t container; /* lj_container */
+  int32_t order;     /* lj_order */
+  int32_t param;     /* k for LJ_ORD_KI, w for LJ_ORD_JSPLIT, else 0 */
+  int32_t newton3;   /* lj_newton3 */
+} lj_config;
+
+/* Create a context for a cubic periodic box.  box[0..2] must be equal (cubic);
+ * cutoff > 0, skin >= 0, cutoff + skin < L/2, eps > 0, sigma > 0.
+ * cuda_stream: a cudaStream_t (may be NULL).  *out receives the context.
+ * Errors: LJ_ERR_ARG, LJ_ERR_CUDA. */
+lj_status lj_init_domain(lj_ctx** out, const double box[3], double cutoff, double skin,
+                         double eps, double sigma, lj_precision prec, void* cuda_stream);
+
+/* Load n particles.  pos: 3*n doubles (SoA), quantised to fixed point as
+ * x_fp = floor(x/L * 2^32) mod 2^32.  vel: 3*n doubles or NULL (zero).
+ * Copies in on the context's stream (host arrays through a device staging
+ * buffer; a pinned host array must not change until the stream has passed the
+ * copy); previous particles are replaced.  Errors: LJ_ERR_ARG (n < 1, null
+ * pos), LJ_ERR_OOM, LJ_ERR_CUDA. */
+lj_status lj_set_particles(lj_ctx* ctx, int64_t n, const double* pos, const double* vel,
+                           double mass, int on_device);
+
+/* As lj_set_particles with positions already in fixed point (3*n uint32). */
+lj_status lj_set_particles_fp(lj_ctx* ctx, int64_t n, const uint32_t* pos_fp, const double* vel,
+                              double mass, int on_device);
+
+/* Bin the particles into the cells of one container by a stable counting sort
+ * on the cell id (Sec. 2.1.1, Linked Cells): cells of edge >= r_c (LJ_LC) or
+ * >= r_c + skin (LJ_VL), n_c = floor(L / edge) per axis, at least 3.  The
+ * library's particle storage is reordered to cell order (ties keep ascending
+ * original index).  Errors: LJ_ERR_STATE, LJ_ERR_ARG (n_c < 3), LJ_ERR_CUDA. */
+lj_status lj_bin_cells(lj_ctx* ctx, int32_t container);
+
+/* Build Verlet lists (Sec. 2.1.1) on the r_c + skin cells: every j != i within
+ * r_c + skin (half_list = 1: only j after i in cell order, for Newton3).
+ * Bins first.  Grows the list capacity and rebuilds on overflow. */
+lj_status lj_build_verlet(lj_ctx* ctx, int32_t half_list);
+
+/* One force evaluation F_i = sum_j F_ij (Eq. 1) with the given configuration.
+ * LC rebins; VL builds the list when it is stale (never built, other half
+ * mode, or a particle moved more than skin/2).  energy_out / virial_out (host,
+ * may be NULL) receive U = sum_pairs U(r) and W = sum_pairs r . F_ij.
+ * Forces stay on the device (lj_get_forces).  Errors: LJ_ERR_ARG (invalid
+ * configuration; see lj_config_valid), LJ_ERR_STATE, LJ_ERR_NONFINITE, LJ_ERR_CUDA. */
+lj_status lj_compute_forces(lj_ctx* ctx, lj_config cfg, double* energy_out, double* virial_out);
+
+/* 1 if cfg is a valid configuration, else 0. */
+int32_t lj_config_valid(lj_config cfg);
+
+/* The valid configurations in a fixed order.  Writes up to cap entries to out
+ * (may be NULL) and returns the total count. */
+int32_t lj_config_list(lj_config* out, int32_t cap);
+
+/* nsteps of velocity Verlet (Sec. 2.1): v += dt/(2m) F; x += v dt (fixed
+ * point, rounded to nearest, periodic wrap); F = F(x) with cfg; v += dt/(2m) F.
+ * Verlet lists are rebuilt every rebuild_every steps (and early when a particle
+ * moved more than skin/2).  Computes the initial forces if none are current.
+ * Errors: as lj_compute_forces. */
+lj_status lj_integrate_step(lj_ctx* ctx, double dt, int32_t nsteps, int32_t rebuild_every,
+                            lj_config cfg);
+
+/* Tuning (Sec. 2.3.2).  kind 0 = full search: every valid configuration is
+ * timed over `samples` force evaluations (CUDA events) and reduced by the
+ * mean; the fastest is returned in *chosen.  kind 1 = learned: the tuner
+ * network (loaded by lj_tuner_set_model) ranks the configurations from the
+ * features (lj_features) and the best predicted one is returned, confirmed by
+ * timing the top `samples` candidates (0 = no timing).  Without a model, kind 1
+ * falls back to the full search.  times_ms (host, may be NULL) receives the
+ * measured mean time of each configuration in lj_config_list order (NaN when
+ * not timed).  Errors: LJ_ERR_STATE, LJ_ERR_ARG, LJ_ERR_CUDA. */
+lj_status lj_tune(lj_ctx* ctx, int32_t kind, int32_t samples, lj_config* chosen, double* times_ms);
+
+/* Full-search selection rule alone (host, no GPU): given `samples` timings per
+ * configuration (row-major [n_cfg][samples], NaN = missing) and a validity
+ * mask, reduce each row (reduce 0 = mean, 1 = minimum) and return the index
+ * of the smallest, or -1 if none is valid. */
+int32_t lj_tune_select(const double* timings, int32_t n_cfg, int32_t samples, const int32_t* valid,
+                       int32_t reduce);
+
+/* The 16 tuner features of the current particles (host out[16]): log density,
+ * log N, mean/std occupancy of the r_c cells, fraction of empty cells, an
+ * 8-bin occupancy histogram (0, 1-2, 3-4, 5-8, 9-16, 17-32, 33-64, >64),
+ * homogeneity (std/mean over 4x4x4 coarse blocks), r_c / cell edge and the
+ * expected Verlet-list length.  Integer statistics are gathered on the device. */
+lj_status lj_features(lj_ctx* ctx, double* out16);
+
+/* Load the learned tuner: an MLP 16-64-64-C (tanh, tanh, linear) with
+ * parameters in the layout W1[64][16] b1[64] W2[64][64] b2[64] W3[C][64]
+ * b3[C] (host, FP32), feature standardisation mean[16] and std[16], and the
+ * C configurations its outputs stand for.  The network predicts log time. */
+lj_status lj_tuner_set_model(lj_ctx* ctx, const float* params, int32_t C, const float* feat_mean,
+                             const float* feat_std, const lj_config* cfgs);
+
+/* The tuner network on the GPU (hand-written FP32 kernels; no counterpart
+ * code in the paper, which proposes data-driven tuning in Sec. 6).  All arrays
+ * are host pointers; each call copies in, runs on the GPU and copies out.
+ * params: the MLP 16-64-64-C parameters (layout as in lj_tuner_set_model).
+ * X: M rows of 16 standardised features; T: M x C target log times;
+ * mask: M x C weights (1 = measured, 0 = missing).  Loss: sum mask (y - T)^2
+ * / sum mask.  stream: a cudaStream_t or NULL (lj_mlp_train uses a stream of
+ * its own and replays one captured epoch as a CUDA graph).
+ * Errors: LJ_ERR_ARG, LJ_ERR_OOM, LJ_ERR_CUDA. */
+lj_status lj_mlp_forward(const float* params, int32_t C, const float* X, int64_t M, float* Y, void* stream);
+lj_status lj_mlp_loss_grad(const float* params, int32_t C, const float* X, const float* T, const float* mask,
+                           int64_t M, float* grad, float* loss, void* stream);
+/* Full-batch Adam (lr, betas 0.9/0.999, eps 1e-8) for `epochs` steps; params
+ * updated in place; losses (may be NULL) receives epochs + 1 values: the loss
+ * before each step and after the last. */
+lj_status lj_mlp_train(const float* X, const float* T, const float* mask, int64_t M, int32_t C, float* params,
+                       int32_t epochs, float lr, float* losses, void* stream);
+
+/* Copy out forces (3*n doubles, original order).  Synchronises if on_device = 0. */
+lj_status lj_get_forces(lj_ctx* ctx, double* dst, int32_t on_device);
+
+/* Copy out positions (fixed point, 3*n uint32) and velocities (3*n doubles),
+ * original order; either pointer may be NULL. */
+lj_status lj_get_state(lj_ctx* ctx, uint32_t* pos_fp, double* vel, int32_t on_device);
+
+/* The pair set of a container, as original-index pairs (i < j) sorted
+ * lexicographically: LJ_LC = pairs within r_c found by the linked-cell scan;
+ * LJ_VL = the entries of the Verlet lists (pairs within r_c + skin).  With
+ * ij == NULL only *n_pairs is set (size query); otherwise ij must hold
+ * 2 * (*n_pairs) int32 on the host. */
+lj_status lj_get_pairs(lj_ctx* ctx, int32_t container, int64_t* n_pairs, int32_t* ij);
+
+/* The current cell order: perm[k] = original index of the k-th particle
+ * (n entries) and cell_start (n_c^3 + 1 entries, n_c of the last binning).
+ * Host pointers; either may be NULL.  *nc_out (may be NULL) gets n_c. */
+lj_status lj_get_cells(lj_ctx* ctx, uint32_t* perm, uint32_t* cell_start, int32_t* nc_out);
+
+/* Verlet lists in cell order: nnbr[n] and the entries nbr[n][cap] (row-major,
+ * sorted j indices in the Sec. 2.1.1 scan order), host pointers; *cap_out
+ * receives the capacity.  Errors: LJ_ERR_STATE if no list was built. */
+lj_status lj_get_verlet(lj_ctx* ctx, int32_t* nbr, int32_t* nnbr, int32_t* cap_out);
+
+/* Counters since the context was created: cnt[0] = force evaluations,
+ * cnt[1] = unique in-cutoff pairs of the last evaluation, cnt[2] = list builds,
+ * cnt[3] = early (skin) rebuilds, cnt[4] = capacity regrowths. */
+lj_status lj_get_counters(lj_ctx* ctx, int64_t* cnt5);
+
+/* Force-kernel timing with CUDA events recorded on the context's stream
+ * around every force-kernel launch (the pair kernel and, for the two-pass
+ * Newton-3 variant, its gather; not the binning or list build).  enable = 1
+ * clears and starts recording, 0 stops.  force_ms / launches (may be NULL)
+ * receive the summed event time and the number of timed evaluations since the
+ * last enable; total_launches (may be NULL) receives the number of kernels this
+ * context has launched.  Synchronises the stream. */
+lj_status lj_timing(lj_ctx* ctx, int32_t enable, double* force_ms, int64_t* launches,
+                    int64_t* total_launches);
+
+/* Kinetic energy 1/2 m sum v^2 of the current state (host out). */
+lj_status lj_kinetic_energy(lj_ctx* ctx, double* ke);
+
+/* Message of the last error on this context (never NULL). */
+const char* lj_last_error(const lj_ctx* ctx);
+
+void lj_destroy(lj_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LJGB_H */

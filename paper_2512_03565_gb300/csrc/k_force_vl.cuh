@@ -1,0 +1,144 @@
+// k_force_vl.cuh -- Verlet-list force functors (Sec. 2.1.1, Verlet lists).
+//
+// The paper leaves Verlet lists out of its pattern study because gathering
+// j's from a list defeats CPU SIMD loads (Sec. 2.1.1); on the GPU a gather
+// per lane is the natural access, and two orders apply:
+//   VL_IPT     one i per lane (V/1 over the list): column-major lists
+//              nbr[k * n + i], so the k-th entries of 32 i's are one
+//              coalesced load.
+//   JSPLIT<w>  w lanes per i striding over its row-major list nbr[i * cap + k]
+//              with a w-lane shuffle reduction (1/V for w = 32, V2/2 for w = 2).
+// With Newton-3 the lists are half lists (j after i in cell order) and every
+// pair's j contribution is scattered with FP64 atomics; the two-pass variant
+// writes each pair's contribution to its list slot and a second kernel sums a
+// particle's slots through the reverse index (see k_verlet.cu) in a fixed order.
+#pragma once
+#include "ljgb_internal.cuh"
+
+namespace ljgb {
+
+struct VLArgs {
+  const uint4* pos;
+  const int32_t* nbr;
+  const int32_t* nnbr;
+  int cap;
+  void* slot;      // two-pass: per-entry j contributions, R[3][cap * n] (column-major slots)
+};
+
+template <typename R>
+__device__ __forceinline__ void vl_atomic(double* p, R v, double scale) {
+  if (v != (R)0) atomicAdd(p, scale * Prec<R>::to_d(v));
+}
+
+// N3: 0 = off, 1 = atomic, 2 = two-pass (pass 1)
+template <typename R, int N3, bool EV>
+__global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut out) {
+  const int64_t n = P.n;
+  double eu_d = 0.0, ew_d = 0.0;
+  int cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool vi = i < n;
+    R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
+    if (vi) {
+      const uint4 pi = A.pos[i];
+      const int m = min(A.nnbr[i], A.cap);
+#pragma unroll 2
+      for (int k = 0; k < m; ++k) {
+        const int j = A.nbr[(int64_t)k * n + i];
+        const uint4 pj = A.pos[j];
+        R af, bf, cf;
+        const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af, bf,
+                                                 cf, eu, ew, cnt);
+        fx += fac * af;
+        fy += fac * bf;
+        fz += fac * cf;
+        if (N3 == 1) {
+          vl_atomic(out.fx + j, fac * af, P.e24u);
+          vl_atomic(out.fy + j, fac * bf, P.e24u);
+          vl_atomic(out.fz + j, fac * cf, P.e24u);
+        } else if (N3 == 2) {
+          const int64_t e = (int64_t)k * n + i;
+          const int64_t ne = (int64_t)A.cap * n;
+          R* sl = (R*)A.slot;
+          sl[e] = fac * af;
+          sl[ne + e] = fac * bf;
+          sl[2 * ne + e] = fac * cf;
+        }
+      }
+      if (N3 == 1) {
+        vl_atomic(out.fx + i, fx, -P.e24u);
+        vl_atomic(out.fy + i, fy, -P.e24u);
+        vl_atomic(out.fz + i, fz, -P.e24u);
+      } else {
+        out.fx[i] = -P.e24u * Prec<R>::to_d(fx);
+        out.fy[i] = -P.e24u * Prec<R>::to_d(fy);
+        out.fz[i] = -P.e24u * Prec<R>::to_d(fz);
+      }
+    }
+    if (EV) {
+      eu_d += Prec<R>::to_d(eu);
+      ew_d += Prec<R>::to_d(ew);
+    }
+  }
+  block_flush<R>(eu_d, ew_d, cnt, out, EV);
+}
+
+template <typename R, int W, int N3, bool EV>
+__global__ void __launch_bounds__(256) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
+  constexpr int G = 32 / W;
+  const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
+  const int64_t n = P.n;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double eu_d = 0.0, ew_d = 0.0;
+  int cnt = 0;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * G < n; w += nwarps) {
+    const int64_t i = w * G + g;
+    const bool vi = i < n;
+    R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
+    if (vi) {
+      const uint4 pi = A.pos[i];
+      const int m = min(A.nnbr[i], A.cap);
+      const int32_t* row = A.nbr + i * A.cap;
+      for (int k = sub; k < m; k += W) {
+        const int j = row[k];
+        const uint4 pj = A.pos[j];
+        R af, bf, cf;
+        const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af, bf,
+                                                 cf, eu, ew, cnt);
+        fx += fac * af;
+        fy += fac * bf;
+        fz += fac * cf;
+        if (N3 == 1) {
+          vl_atomic(out.fx + j, fac * af, P.e24u);
+          vl_atomic(out.fy + j, fac * bf, P.e24u);
+          vl_atomic(out.fz + j, fac * cf, P.e24u);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, o);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (vi && sub == 0) {
+      if (N3 == 1) {
+        vl_atomic(out.fx + i, fx, -P.e24u);
+        vl_atomic(out.fy + i, fy, -P.e24u);
+        vl_atomic(out.fz + i, fz, -P.e24u);
+      } else {
+        out.fx[i] = -P.e24u * Prec<R>::to_d(fx);
+        out.fy[i] = -P.e24u * Prec<R>::to_d(fy);
+        out.fz[i] = -P.e24u * Prec<R>::to_d(fz);
+      }
+    }
+    if (EV) {
+      eu_d += Prec<R>::to_d(eu);
+      ew_d += Prec<R>::to_d(ew);
+    }
+  }
+  block_flush<R>(eu_d, ew_d, cnt, out, EV);
+}
+
+}  // namespace ljgb

@@ -1,0 +1,199 @@
+// k_integrate.cu -- velocity Verlet (Sec. 2.1: Verlet integration of Newton's
+// equations), reorder back to the caller's particle order, tuner feature
+// statistics, and small reductions.
+#include "k_force_lc.cuh"
+
+namespace ljgb {
+
+static inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// v = fma(dt/2m, F, v) (one rounding); with drift, x += rne(v * dtu) mod 2^32,
+// where rne(v * dtu) is the exact product rounded once to the nearest integer:
+// fma(v, dtu, 1.5 * 2^52) lies in [2^52, 2^53) where the spacing is 1, and its
+// low 32 bits are the displacement modulo 2^32.  With track, particles whose
+// displacement since the last list build exceeds skin/2 set ST_SKIN.
+__global__ void k_kick_drift(uint4* __restrict__ pos, double* __restrict__ vel, const double* __restrict__ frc,
+                             int64_t n, double hdtm, double dtu, int drift, const uint32_t* __restrict__ xb,
+                             uint64_t disp2_max, uint32_t* __restrict__ status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v0 = __fma_rn(hdtm, frc[i], vel[i]);
+  double v1 = __fma_rn(hdtm, frc[n + i], vel[n + i]);
+  double v2 = __fma_rn(hdtm, frc[2 * n + i], vel[2 * n + i]);
+  vel[i] = v0;
+  vel[n + i] = v1;
+  vel[2 * n + i] = v2;
+  if (!drift) return;
+  const double M = 6755399441055744.0;  // 1.5 * 2^52
+  uint4 p = pos[i];
+  p.x += (uint32_t)__double2loint(__fma_rn(v0, dtu, M));
+  p.y += (uint32_t)__double2loint(__fma_rn(v1, dtu, M));
+  p.z += (uint32_t)__double2loint(__fma_rn(v2, dtu, M));
+  pos[i] = p;
+  if (xb) {
+    const int a = (int)(p.x - xb[i]), b = (int)(p.y - xb[n + i]), c = (int)(p.z - xb[2 * n + i]);
+    const uint64_t d2 = (uint64_t)((long long)a * a) + (uint64_t)((long long)b * b) + (uint64_t)((long long)c * c);
+    if (d2 > disp2_max) atomicOr(status, ST_SKIN);
+  }
+}
+
+cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track) {
+  const double half_skin_u = 0.5 * c.skin * 4294967296.0 / c.L;
+  const double d2 = half_skin_u * half_skin_u;
+  const uint64_t d2max = d2 >= 1.8e19 ? ~0ull : (uint64_t)d2;
+  k_kick_drift<<<nb(c.n, 256), 256, 0, c.stream>>>(c.pos, c.vel, c.frc, c.n, hdtm, dtu, kick_only ? 0 : 1,
+                                                   track ? c.x_build : nullptr, d2max, c.status);
+  return cudaGetLastError();
+}
+
+// dst[a][orig(s)] = src[a][s]
+__global__ void k_to_original(const uint4* __restrict__ pos, const double* __restrict__ src, int64_t n,
+                              double* __restrict__ dst) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t o = pos[s].w;
+  dst[o] = src[s];
+  dst[n + o] = src[n + s];
+  dst[2 * n + o] = src[2 * n + s];
+}
+
+__global__ void k_pos_to_original(const uint4* __restrict__ pos, int64_t n, uint32_t* __restrict__ dst) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint4 p = pos[s];
+  dst[p.w] = p.x;
+  dst[n + p.w] = p.y;
+  dst[2 * n + p.w] = p.z;
+}
+
+cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s) {
+  k_to_original<<<nb(n, 256), 256, 0, s>>>(pos, src3, n, dst3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s) {
+  k_pos_to_original<<<nb(n, 256), 256, 0, s>>>(pos, n, dst3);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Tuner feature statistics (exact integers): per-cell counts on the r_c cells,
+// then sum occ, sum occ^2, the 8-bin occupancy histogram and the 64
+// coarse-block counts (top two bits of each coordinate).
+// stats layout: [0] sum occ, [1] sum occ^2, [2..9] histogram, [10..73] blocks.
+// ---------------------------------------------------------------------------
+__global__ void k_feat_count(const uint4* __restrict__ pos, int64_t n, uint32_t nc, uint32_t* __restrict__ occ,
+                             unsigned long long* __restrict__ stats) {
+  __shared__ unsigned int s_blk[64];
+  if (threadIdx.x < 64) s_blk[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint4 p = pos[i];
+    const uint32_t c = (cx_of(p.z, nc) * nc + cx_of(p.y, nc)) * nc + cx_of(p.x, nc);
+    atomicAdd(&occ[c], 1u);
+    atomicAdd(&s_blk[((p.z >> 30) * 4 + (p.y >> 30)) * 4 + (p.x >> 30)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 64 && s_blk[threadIdx.x]) atomicAdd(&stats[10 + threadIdx.x], (unsigned long long)s_blk[threadIdx.x]);
+}
+
+__global__ void k_feat_cells(const uint32_t* __restrict__ occ, int64_t ncell, unsigned long long* __restrict__ stats) {
+  __shared__ unsigned long long s_acc[10];
+  if (threadIdx.x < 10) s_acc[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long s1 = 0, s2 = 0;
+  unsigned int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long o = occ[c];
+    s1 += o;
+    s2 += o * o;
+    const int b = o == 0 ? 0 : o <= 2 ? 1 : o <= 4 ? 2 : o <= 8 ? 3 : o <= 16 ? 4 : o <= 32 ? 5 : o <= 64 ? 6 : 7;
+    h[b] += 1;
+  }
+  atomicAdd(&s_acc[0], s1);
+  atomicAdd(&s_acc[1], s2);
+#pragma unroll
+  for (int b = 0; b < 8; ++b)
+    if (h[b]) atomicAdd(&s_acc[2 + b], (unsigned long long)h[b]);
+  __syncthreads();
+  if (threadIdx.x < 10 && s_acc[threadIdx.x]) atomicAdd(&stats[threadIdx.x], s_acc[threadIdx.x]);
+}
+
+cudaError_t launch_feature_stats(Ctx& c, unsigned long long* stats) {
+  const int nc = c.nc_lc;
+  const int64_t ncell = (int64_t)nc * nc * nc;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(stats, 0, 74 * sizeof(unsigned long long), c.stream)) != cudaSuccess) return e;
+  // the per-cell counter array of the binning is free between binnings
+  if (c.cnt_cap < (size_t)ncell + 1) {
+    if (c.cnt) cudaFree(c.cnt);
+    c.cnt = nullptr;
+    c.cnt_cap = 0;
+    if ((e = cudaMalloc(&c.cnt, ((size_t)ncell + 1) * sizeof(uint32_t))) != cudaSuccess) return e;
+    c.cnt_cap = (size_t)ncell + 1;
+  }
+  if ((e = cudaMemsetAsync(c.cnt, 0, (size_t)ncell * sizeof(uint32_t), c.stream)) != cudaSuccess) return e;
+  k_feat_count<<<nb(c.n, 256), 256, 0, c.stream>>>(c.pos, c.n, (uint32_t)nc, c.cnt, stats);
+  k_feat_cells<<<(unsigned)std::min<int64_t>(nb(ncell, 256), 1024), 256, 0, c.stream>>>(c.cnt, ncell, stats);
+  return cudaGetLastError();
+}
+
+// 1/2 m sum v^2 (FP64)
+__global__ void k_ke(const double* __restrict__ vel, int64_t n, double* __restrict__ out) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x)
+    s += vel[i] * vel[i];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+cudaError_t launch_ke(Ctx& c, double* out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), c.stream);
+  if (e != cudaSuccess) return e;
+  k_ke<<<std::min<unsigned>(nb(3 * c.n, 256), 1024), 256, 0, c.stream>>>(c.vel, c.n, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_check_finite(const double* __restrict__ f, int64_t m, uint32_t* __restrict__ status) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(f[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+cudaError_t launch_check_finite(Ctx& c) {
+  k_check_finite<<<std::min<unsigned>(nb(3 * c.n, 256), 1024), 256, 0, c.stream>>>(c.frc, 3 * c.n, c.status);
+  return cudaGetLastError();
+}
+
+// Pair set of the linked-cell scan: every (i, j) with orig(i) < orig(j),
+// 0 < R^2 <= Rc2, j in the 27 cells around i.  With out == nullptr only counts.
+__global__ void k_lc_pairs(const uint4* __restrict__ pos, const uint32_t* __restrict__ cs, int nc, int64_t n,
+                           uint64_t Rc2, unsigned long long* __restrict__ count, int2* __restrict__ out,
+                           unsigned long long cap) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 pi = pos[i];
+  const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
+  Seg segs[18];
+  const int ns = make_segments<false>(cs, nc, cz * nc + cy, cx, cx, 0u, segs);
+  for (int s = 0; s < ns; ++s)
+    for (uint32_t j = segs[s].b; j < segs[s].e; ++j) {
+      const uint4 pj = pos[j];
+      if (pj.w <= pi.w) continue;
+      if (!in_cut_exact(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), Rc2)) continue;
+      const unsigned long long k = atomicAdd(count, 1ull);
+      if (out && k < cap) out[k] = make_int2((int)pi.w, (int)pj.w);
+    }
+}
+
+cudaError_t launch_lc_pairs(Ctx& c, unsigned long long* count, int2* out, size_t cap) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), c.stream);
+  if (e != cudaSuccess) return e;
+  k_lc_pairs<<<nb(c.n, 128), 128, 0, c.stream>>>(c.pos, c.cell_start, c.binned_nc, c.n, c.P.Rc2, count, out,
+                                                (unsigned long long)cap);
+  return cudaGetLastError();
+}
+
+}  // namespace ljgb

@@ -1,0 +1,389 @@
+// ljgb_internal.cuh -- shared definitions of the CUDA library (device helpers,
+// parameter block, context).  Not part of the public ABI (include/ljgb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/ljgb.h"
+
+namespace ljgb {
+
+// ---------------------------------------------------------------------------
+// Device status word bits (sticky until read by the host).
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+  ST_CAPACITY = 1u,   // a Verlet list overflowed
+  ST_SKIN = 2u,       // a particle moved more than skin/2 since the list build
+  ST_NONFINITE = 4u,  // NaN/Inf force
+  ST_OOB = 8u,        // index out of range (defensive checks)
+  ST_TIMEOUT = 16u,   // a bounded wait gave up
+};
+
+// ---------------------------------------------------------------------------
+// Parameter block, passed by value to the force kernels.
+//
+// Distances are handled in fixed-point units u = L / 2^32 (Sec. 2.1 cutoff
+// rule read as an exact integer test).  The pair kernel works with
+// r2u = R^2 in units u^2 and the dimensionless s2 = sigma^2 / r^2 = S / r2u,
+// S = sigma^2 / u^2.  The force on i is F_i = -(24 eps / u) sum_j fac'_ij a_ij
+// with fac' = s6 (2 s6 - 1) / r2u and a_ij the fixed-point difference, which
+// equals the textbook -(24 eps / r^2) s6 (2 s6 - 1) dx.
+// ---------------------------------------------------------------------------
+struct LJParams {
+  int32_t n;          // particles
+  int32_t nc;         // cells per axis of the active container
+  uint64_t Rc2;       // floor((r_c/u)^2)
+  float rc2f_lo, rc2f_hi;    // FP32 decision band around Rc2 (exact test inside)
+  double rc2d_lo, rc2d_hi;   // FP64 decision band
+  float S_hi, S_lo;   // S = sigma^2/u^2 as an unevaluated float sum
+  double S;           // S in FP64
+  double e24u;        // 24 eps / u
+  double e24;         // 24 eps
+  double e4;          // 4 eps
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers.
+// ---------------------------------------------------------------------------
+
+// Exact conversion of an FP32 value to FP64 done with integer operations on
+// the IEEE-754 bit fields (sign kept, exponent rebiased 127 -> 1023, mantissa
+// shifted into place).  GB300's FP64 pipe runs at ~1/80 of FP32 and hardware
+// float->double conversions at under one per clock per SM, so the per-particle
+// FP64 fold uses this instead.  FP32 subnormals (|x| < 1.2e-38) become signed
+// zero; Inf and NaN are preserved.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint32_t m = b & 0x7fffffu;
+  const uint32_t sgn = b & 0x80000000u;
+  uint32_t ex = (e == 255u) ? 0x7ffu : (e + 896u);
+  uint32_t hi = sgn | (ex << 20) | (m >> 3);
+  uint32_t lo = m << 29;
+  hi = (e == 0u) ? sgn : hi;
+  lo = (e == 0u) ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over aligned groups of W lanes (W a power of two <= 32); every lane of a
+// group ends with the group's total.
+template <int W>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Exact membership test: 0 < R^2 <= Rc2 with R^2 in 64-bit integers.
+__device__ __forceinline__ bool in_cut_exact(int a, int b, int c, uint64_t Rc2) {
+  const uint64_t R2 = (uint64_t)((long long)a * a) + (uint64_t)((long long)b * b) +
+                      (uint64_t)((long long)c * c);
+  return (R2 != 0ull) & (R2 <= Rc2);
+}
+
+// 1/x for positive normal x: the hardware approximation refined by one
+// Newton-Raphson step x0 (2 - x x0), written as two fused multiply-adds.
+__device__ __forceinline__ float rcp_nr(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  const float e = fmaf(-x, y, 1.0f);
+  return fmaf(y, e, y);
+}
+
+// ---------------------------------------------------------------------------
+// The pair kernel (Algorithm 1's ForceKernel), FP32 and FP64 variants.
+//
+// Input: the fixed-point difference (a,b,c) = x_j - x_i (minimum image).
+// Output: fac' (0 when the pair is outside the cutoff) and the converted
+// differences; the caller accumulates fac' * (af,bf,cf).  With EV it also
+// accumulates s6 (s6 - 1) (energy / 4 eps) and s6 (2 s6 - 1) (virial / 24 eps).
+// ---------------------------------------------------------------------------
+template <bool EV>
+__device__ __forceinline__ float pair_f32(int a, int b, int c, const LJParams& P, float& af, float& bf,
+                                          float& cf, float& eu, float& ew, int& cnt) {
+  af = __int2float_rn(a);
+  bf = __int2float_rn(b);
+  cf = __int2float_rn(c);
+  const float r2 = fmaf(cf, cf, fmaf(bf, bf, af * af));
+  bool in = (r2 < P.rc2f_lo) & (r2 > 0.0f);
+  if ((r2 >= P.rc2f_lo) & (r2 <= P.rc2f_hi)) in = in_cut_exact(a, b, c, P.Rc2);
+  float fac = 0.0f;
+  if (in) {
+    const float inv = rcp_nr(r2);
+    const float s2 = fmaf(inv, P.S_hi, inv * P.S_lo);
+    const float s6 = s2 * s2 * s2;
+    const float t = fmaf(2.0f, s6, -1.0f);
+    fac = s6 * t * inv;
+    if (EV) {
+      eu += fmaf(s6, s6, -s6);
+      ew += s6 * t;
+    }
+    cnt += 1;
+  }
+  return fac;
+}
+
+template <bool EV>
+__device__ __forceinline__ double pair_f64(int a, int b, int c, const LJParams& P, double& ad,
+                                           double& bd, double& cd, double& eu, double& ew, int& cnt) {
+  ad = (double)a;
+  bd = (double)b;
+  cd = (double)c;
+  const double r2 = fma(cd, cd, fma(bd, bd, ad * ad));
+  bool in = (r2 < P.rc2d_lo) & (r2 > 0.0);
+  if ((r2 >= P.rc2d_lo) & (r2 <= P.rc2d_hi)) in = in_cut_exact(a, b, c, P.Rc2);
+  double fac = 0.0;
+  if (in) {
+    const double inv = 1.0 / r2;
+    const double s2 = P.S * inv;
+    const double s6 = s2 * s2 * s2;
+    const double t = fma(2.0, s6, -1.0);
+    fac = s6 * t * inv;
+    if (EV) {
+      eu += fma(s6, s6, -s6);
+      ew += s6 * t;
+    }
+    cnt += 1;
+  }
+  return fac;
+}
+
+// Precision traits: the accumulator type of a pair chunk and its FP64 fold.
+template <typename R>
+struct Prec;
+template <>
+struct Prec<float> {
+  template <bool EV>
+  __device__ __forceinline__ static float pair(int a, int b, int c, const LJParams& P, float& af, float& bf,
+                                               float& cf, float& eu, float& ew, int& cnt) {
+    return pair_f32<EV>(a, b, c, P, af, bf, cf, eu, ew, cnt);
+  }
+  __device__ __forceinline__ static double to_d(float v) { return f2d_exact(v); }
+};
+template <>
+struct Prec<double> {
+  template <bool EV>
+  __device__ __forceinline__ static double pair(int a, int b, int c, const LJParams& P, double& ad,
+                                                double& bd, double& cd, double& eu, double& ew, int& cnt) {
+    return pair_f64<EV>(a, b, c, P, ad, bd, cd, eu, ew, cnt);
+  }
+  __device__ __forceinline__ static double to_d(double v) { return v; }
+};
+
+__device__ __forceinline__ int mimg(uint32_t xi, uint32_t xj) { return (int)(xj - xi); }
+
+// Output block of a force evaluation: sorted-order FP64 forces plus global
+// accumulators.
+struct ForceOut {
+  double* fx;
+  double* fy;
+  double* fz;
+  double* ev;             // [0] = sum s6(s6-1), [1] = sum s6(2s6-1) (each pair counted per side visited)
+  unsigned long long* npairs;  // pair evaluations counted (per side visited)
+  uint32_t* status;
+};
+
+// Block-level reduction of the energy/virial partials and pair counts; one
+// atomic per block.  Every thread of the block must call it.
+template <typename R>
+__device__ __forceinline__ void block_flush(double eu, double ew, int cnt, const ForceOut& out, bool EV) {
+  __shared__ double s_e[2][32];
+  __shared__ unsigned long long s_c[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  unsigned long long c = (unsigned long long)cnt;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (EV) {
+    eu = warp_sum_d(eu);
+    ew = warp_sum_d(ew);
+  }
+  if (lane == 0) {
+    s_c[wid] = c;
+    if (EV) {
+      s_e[0][wid] = eu;
+      s_e[1][wid] = ew;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tc = 0;
+    double te = 0.0, tw = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      tc += s_c[w];
+      if (EV) {
+        te += s_e[0][w];
+        tw += s_e[1][w];
+      }
+    }
+    atomicAdd(out.npairs, tc);
+    if (EV) {
+      atomicAdd(&out.ev[0], te);
+      atomicAdd(&out.ev[1], tw);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side context.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+struct Ctx {
+  // geometry and model
+  double L = 0, rc = 0, skin = 0, eps = 1, sigma = 1, mass = 1;
+  int prec = LJ_PREC_FP32_ACC64;
+  cudaStream_t stream = nullptr;
+  int nc_lc = 0, nc_vl = 0;
+  LJParams P{};            // params with the cutoff r_c
+  uint64_t Rl2 = 0;        // floor((r_l/u)^2)
+  int64_t n = 0;
+  bool have_particles = false;
+  bool moved = true;             // particles moved since the last binning
+  bool moved_since_build = true; // particles moved since the last list build
+  lj_config last_cfg{-1, -1, -1, -1};
+  double np_side = 1.0;          // pair-count scale of the pending evaluation
+  bool np_pending = false;
+  int rebuild_every = 10;        // list period assumed by the tuner's cost
+
+  // particle state in the current (cell) order
+  uint4* pos = nullptr;    // x, y, z fixed point, w = original index
+  uint4* pos_alt = nullptr;
+  double* vel = nullptr;   // [3][n]
+  double* vel_alt = nullptr;
+  double* frc = nullptr;   // [3][n] forces of the last evaluation
+  double* frc_alt = nullptr;
+  bool forces_valid = false;
+
+  // binning
+  int binned_nc = 0;       // n_c of the current cell order (0 = not binned)
+  int binned_for = -1;     // container the order belongs to
+  uint32_t* cell_start = nullptr;
+  size_t cell_cap = 0;     // capacity of cell_start (entries)
+  uint32_t* cnt = nullptr; // per-cell counters
+  size_t cnt_cap = 0;
+  uint32_t* cell_of = nullptr;
+  uint32_t* slot = nullptr;
+  unsigned long long* key = nullptr;  // (orig << 32) | source slot
+  uint32_t* scan_tmp = nullptr;
+  size_t scan_tmp_cap = 0;
+
+  // tiles of the linked-cell kernels (per tile size)
+  int tiles_T = 0;
+  int tiles_for_nc = 0;
+  uint64_t tiles_gen = 0;
+  uint4* tiles = nullptr;  // (begin, end, row, cx_first | cx_last << 16)
+  size_t tiles_cap = 0;
+  int ntiles = 0;
+  uint32_t* row_tiles = nullptr;  // per row tile counts / offsets
+  size_t row_tiles_cap = 0;
+  uint64_t bin_gen = 0;    // increments at every binning
+  uint32_t* tile_ctr = nullptr;  // device work counter of the tile kernels
+
+  // Verlet lists
+  int32_t* nbr = nullptr;  // row-major [n][cap] (JSPLIT) or column-major [cap][n] (IPT)
+  int32_t* nnbr = nullptr;
+  int vl_cap = 0;
+  int vl_half = -1;        // half mode of the current list, -1 = none
+  int vl_colmajor = 0;
+  bool vl_valid = false;
+  uint32_t* x_build = nullptr;  // [3][n] positions at the last build
+  uint32_t* maxdisp = nullptr;  // device max |displacement| (units)
+  int steps_since_build = 0;
+
+  // two-pass Newton-3: per-entry slots R[3][cap*n] and the reverse index
+  void* twopass = nullptr;
+  size_t twopass_bytes = 0;
+  uint32_t* rev_cnt = nullptr;    // n + 1
+  uint32_t* rev_start = nullptr;  // n + 1
+  uint32_t* rev_slot = nullptr;   // cap * n
+  unsigned long long* rev_key = nullptr;   // cap * n
+  unsigned long long* rev_key2 = nullptr;  // cap * n
+  size_t rev_cap = 0;             // entries allocated in rev_slot / rev_key
+  bool rev_valid = false;
+  uint32_t* maxlen = nullptr;     // device: longest list of the last build
+
+  // accumulators and status
+  double* ev = nullptr;    // 2 doubles
+  unsigned long long* npairs = nullptr;
+  uint32_t* status = nullptr;
+  double* host_ev = nullptr;  // pinned mirror
+  unsigned long long* host_np = nullptr;
+  uint32_t* host_status = nullptr;
+
+  // staging buffer for host uploads
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+
+  // feature statistics scratch
+  unsigned long long* feat_stats = nullptr;
+
+  // learned tuner
+  std::vector<float> mlp_params;
+  int mlp_C = 0;
+  std::vector<float> mlp_mean, mlp_std;
+  std::vector<lj_config> mlp_cfgs;
+
+  // counters
+  int64_t counters[5] = {0, 0, 0, 0, 0};
+  int64_t launches = 0;          // kernels launched by this context
+  // optional CUDA-event timing of the force kernel (lj_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (one translation unit each).
+// ---------------------------------------------------------------------------
+cudaError_t launch_quantize(const double* pos, int64_t n, double L, const double* vel, uint4* out_pos,
+                            double* out_vel, cudaStream_t s);
+cudaError_t launch_load_fp(const uint32_t* pos_fp, int64_t n, const double* vel, uint4* out_pos, double* out_vel,
+                           cudaStream_t s);
+cudaError_t bin_cells(Ctx& c, int nc);
+cudaError_t build_tiles(Ctx& c, int T);
+cudaError_t excl_scan_u32(Ctx& c, const uint32_t* in, uint32_t* out, int64_t n);
+cudaError_t sort_segments(Ctx& c, const uint32_t* starts, int64_t nseg, unsigned long long* key,
+                          unsigned long long* key2);
+cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen);
+cudaError_t launch_reverse_index(Ctx& c);
+cudaError_t launch_twopass_gather(Ctx& c);
+cudaError_t force_lc_f32(Ctx& c, const lj_config& cfg, bool ev);
+cudaError_t force_lc_f64(Ctx& c, const lj_config& cfg, bool ev);
+cudaError_t force_vl_f32(Ctx& c, const lj_config& cfg, bool ev);
+cudaError_t force_vl_f64(Ctx& c, const lj_config& cfg, bool ev);
+cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track);
+cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s);
+cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s);
+cudaError_t launch_feature_stats(Ctx& c, unsigned long long* stats);
+cudaError_t launch_ke(Ctx& c, double* out);
+cudaError_t launch_check_finite(Ctx& c);
+cudaError_t launch_lc_pairs(Ctx& c, unsigned long long* count, int2* out, size_t cap);
+
+}  // namespace ljgb
+
+// The opaque handle of the C ABI.
+struct lj_ctx {
+  ljgb::Ctx c;
+};

@@ -1,0 +1,101 @@
+"""CPU-only checks of the C ABI library: it loads without a GPU, exports every
+entry point include/ljgb.h declares, validates arguments on the host, and its
+host-side tuning rule (Sec. 2.3.2 full search: reduce each configuration's
+samples, take the fastest) picks the argmin of injected fake timings."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lj():
+    from paper_2512_03565_gb300 import build as b
+    b.build()
+    from paper_2512_03565_gb300 import ljgb
+    ljgb.load()
+    return ljgb
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "ljgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lj_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(lj):
+    lib = C.CDLL(lj.LIB_PATH)
+    names = header_symbols()
+    assert len(names) >= 25
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(lj.exported_symbols()) == set(names)
+
+
+def test_init_domain_rejects_bad_arguments_on_host(lj):
+    lib = lj.load()
+    h = C.c_void_p()
+    box = (C.c_double * 3)(10.0, 10.0, 10.0)
+    bad = [
+        ((C.c_double * 3)(10.0, 11.0, 10.0), 2.5, 0.3),   # not cubic
+        (box, 0.0, 0.3),                                  # cutoff <= 0
+        (box, 2.5, -0.1),                                 # negative skin
+        (box, 4.0, 1.1),                                  # rc + skin >= L/2
+    ]
+    for b, rc, skin in bad:
+        assert lib.lj_init_domain(C.byref(h), b, rc, skin, 1.0, 1.0, 1, None) == lj.LJ_ERR_ARG
+    assert lib.lj_init_domain(C.byref(h), box, 2.5, 0.3, 0.0, 1.0, 1, None) == lj.LJ_ERR_ARG
+    assert lib.lj_init_domain(C.byref(h), box, 2.5, 0.3, 1.0, 1.0, 7, None) == lj.LJ_ERR_ARG
+    assert lib.lj_init_domain(None, box, 2.5, 0.3, 1.0, 1.0, 1, None) == lj.LJ_ERR_ARG
+
+
+def test_config_space(lj):
+    cfgs = lj.configs()
+    names = [lj.config_name(c) for c in cfgs]
+    assert len(names) == len(set(names)) == 33
+    assert all(lj.load().lj_config_valid(c) for c in cfgs)
+    # invalid combinations are masked (cf. the paper's lc_c01, usable only without Newton3)
+    for bad in [lj.config(lj.LJ_LC, lj.LJ_ORD_VL_IPT), lj.config(lj.LJ_LC, lj.LJ_ORD_KI, 3),
+                lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, 64), lj.config(lj.LJ_LC, lj.LJ_ORD_IPT_SMEM, 0, 2),
+                lj.config(lj.LJ_VL, lj.LJ_ORD_ROT32), lj.config(lj.LJ_VL, lj.LJ_ORD_JSPLIT, 4, 2),
+                lj.config(2, 0)]:
+        assert not lj.load().lj_config_valid(bad)
+
+
+def test_tune_select_is_argmin_of_reduced_evidence(lj):
+    rng = np.random.default_rng(3)
+    for reduce in (0, 1):
+        for _ in range(50):
+            n_cfg, s = rng.integers(2, 40), rng.integers(1, 10)
+            t = rng.uniform(0.1, 5.0, size=(n_cfg, s))
+            t[rng.random((n_cfg, s)) < 0.1] = np.nan
+            valid = (rng.random(n_cfg) < 0.8).astype(np.int32)
+            red = np.where(np.isnan(t), np.inf if reduce else 0.0, t)
+            cnt = (~np.isnan(t)).sum(1)
+            v = red.min(1) if reduce else np.where(cnt > 0, red.sum(1) / np.maximum(cnt, 1), np.inf)
+            v = np.where((valid == 1) & (cnt > 0), v, np.inf)
+            want = int(np.argmin(v)) if np.isfinite(v).any() else -1
+            assert lj.tune_select(t, valid, reduce) == want
+
+
+def test_tune_select_edge_cases(lj):
+    assert lj.tune_select(np.full((3, 2), np.nan)) == -1
+    assert lj.tune_select(np.array([[1.0], [1.0], [0.5]]), np.array([1, 1, 0])) == 0   # ties keep the first
+    assert lj.tune_select(np.array([[2.0, 0.1], [1.0, 1.0]]), reduce=1) == 0
+    assert lj.tune_select(np.array([[2.0, 0.1], [1.0, 1.0]]), reduce=0) == 1
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import importlib
+    from paper_2512_03565_gb300 import ljgb
+    mod = importlib.reload(ljgb)
+    monkeypatch.setattr(mod, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(mod, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        mod.load()
+    importlib.reload(ljgb)

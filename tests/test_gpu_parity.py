@@ -1,0 +1,312 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (from the required accuracy of the force path): forces
+max_i |F_i - F_i^oracle| / RMS_i |F_i^oracle| <= 1e-12 with FP64 pair math and
+<= 1e-5 with FP32 pair math and FP64 accumulation; energies |dU|/|U| <= 1e-12 /
+1e-6.  Cell order, pair sets and Verlet lists are integer results: bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_03565_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+ETOL = {0: 1e-12, 1: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def lj():
+    from paper_2512_03565_gb300 import build as b
+    b.build()
+    oracle.build()
+    from paper_2512_03565_gb300 import ljgb
+    ljgb.load()
+    return ljgb
+
+
+def rel_err(F, Fref):
+    rms = np.sqrt((Fref ** 2).sum(0).mean())
+    return np.abs(F - Fref).max() / rms
+
+
+def ref_forces(s, rc=None):
+    return oracle.forces_bruteforce(s.pos, s.L, rc or s.rc)
+
+
+@pytest.fixture(scope="module")
+def sys_small():
+    return W.stratified(6000, 0.75, 101)
+
+
+@pytest.fixture(scope="module")
+def ref_small(sys_small):
+    return ref_forces(sys_small)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_config_matches_oracle(lj, sys_small, ref_small, prec):
+    s = sys_small
+    F_ref, U_ref, W_ref, np_ref = ref_small
+    d = lj.Domain(s.L, s.rc, s.skin, precision=prec)
+    d.set_particles(s.pos, s.vel)
+    bad = []
+    for cfg in lj.configs():
+        U, Wv = d.compute_forces(cfg, energy=True)
+        err = rel_err(d.forces(), F_ref)
+        eU = abs(U - U_ref) / abs(U_ref)
+        eW = abs(Wv - W_ref) / abs(W_ref)
+        npairs = d.counters()[1]
+        if not (err <= TOL[prec] and eU <= ETOL[prec] and eW <= ETOL[prec] and npairs == np_ref):
+            bad.append((lj.config_name(cfg), err, eU, eW, npairs, np_ref))
+    d.close()
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config1_uniform_1000(lj, prec):
+    """1,000 particles, uniform random at density 0.8, rc 2.5, one evaluation."""
+    s = W.config1()
+    F_ref, U_ref, _, np_ref = ref_forces(s)
+    assert abs(np_ref - 26180) < 800
+    d = lj.Domain(s.L, s.rc, s.skin, precision=prec)
+    d.set_particles(s.pos, s.vel)
+    for cfg in [lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, 32), lj.config(lj.LJ_LC, lj.LJ_ORD_IPT_SMEM, 0, 1),
+                lj.config(lj.LJ_LC, lj.LJ_ORD_ROT32, 0, 1), lj.config(lj.LJ_VL, lj.LJ_ORD_VL_IPT, 0, 2)]:
+        if prec == 1:
+            # uniform random start has overlaps down to r ~ 0.05 (|F| ~ 1e17): FP32 pair
+            # math stays finite there but only the FP64 path is held to a tolerance
+            U, _ = d.compute_forces(cfg, energy=True)
+            assert np.isfinite(d.forces()).all()
+            continue
+        U, _ = d.compute_forces(cfg, energy=True)
+        assert rel_err(d.forces(), F_ref) <= TOL[0], lj.config_name(cfg)
+        assert abs(U - U_ref) <= ETOL[0] * abs(U_ref)
+        assert d.counters()[1] == np_ref
+    d.close()
+
+
+def test_cells_and_pairs_bit_exact(lj, sys_small):
+    s = sys_small
+    d = lj.Domain(s.L, s.rc, s.skin)
+    d.set_particles(s.pos, s.vel)
+    for cont, r in [(lj.LJ_LC, s.rc), (lj.LJ_VL, s.rc + s.skin)]:
+        d.bin_cells(cont)
+        perm, cs, nc = d.cells()
+        assert nc == oracle.ncells(s.L, r)
+        perm_ref, cs_ref = oracle.bin_cells(s.pos, nc)
+        assert np.array_equal(perm, perm_ref) and np.array_equal(cs, cs_ref)
+    assert np.array_equal(d.pairs(lj.LJ_LC), oracle.pairs_bruteforce(s.pos, s.L, s.rc))
+    for half in (0, 1):
+        d.build_verlet(half)
+        assert np.array_equal(d.pairs(lj.LJ_VL), oracle.pairs_bruteforce(s.pos, s.L, s.rc + s.skin))
+        nbr, nn = d.verlet()
+        nc = oracle.ncells(s.L, s.rc + s.skin)
+        _, _, nbr_ref, nn_ref, _ = oracle.verlet(s.pos, s.L, s.rc + s.skin, nc, half, nbr.shape[1])
+        assert np.array_equal(nn, nn_ref)
+        for i in range(s.n):                  # same entries in the same scan order
+            assert np.array_equal(nbr[i, :nn[i]], nbr_ref[i, :nn[i]])
+    d.close()
+
+
+def edge_cases():
+    rng = np.random.default_rng(99)
+    out = []
+    for L, n in [(3.3, 20), (4.0, 60), (5.0, 120), (3.0, 90)]:
+        out.append(("uniform", L, rng.integers(0, 2 ** 32, size=(3, n), dtype=np.uint64).astype(np.uint32)))
+    out.append(("one_cell", 4.0, rng.integers(0, 2 ** 30, size=(3, 50), dtype=np.uint64).astype(np.uint32)))
+    faces = rng.integers(0, 4, size=(3, 64)).astype(np.uint64) * 2 ** 30
+    faces[:, :8] = 0
+    out.append(("faces", 4.0, faces.astype(np.uint32)))
+    out.append(("octant", 5.0, rng.integers(0, 2 ** 31, size=(3, 80), dtype=np.uint64).astype(np.uint32)))
+    L = 4.0
+    dfp = int(round(1.0 / (L / 2 ** 32)))
+    out.append(("at_cutoff", L, np.array([[0, dfp, 0, 2 ** 31], [0, 0, dfp + 1, 2 ** 31], [0, 0, 0, 0]], dtype=np.uint32)))
+    big = rng.integers(0, 2 ** 30, size=(3, 300), dtype=np.uint64).astype(np.uint32)   # 300 in one cell
+    out.append(("crowded_cell", 4.0, big))
+    return out
+
+
+@pytest.mark.parametrize("name,L,pos", edge_cases(), ids=[c[0] for c in edge_cases()])
+def test_edge_cases_fp64(lj, name, L, pos):
+    rc, skin = 1.0, 0.0
+    F_ref, U_ref, _, np_ref = oracle.forces_bruteforce(pos, L, rc)
+    d = lj.Domain(L, rc, skin, precision=lj.LJ_PREC_FP64)
+    d.set_particles(pos)
+    assert np.array_equal(d.pairs(lj.LJ_LC), oracle.pairs_bruteforce(pos, L, rc))
+    for cfg in lj.configs():
+        U, _ = d.compute_forces(cfg, energy=True)
+        F = d.forces()
+        scale = max(np.sqrt((F_ref ** 2).sum(0).mean()), 1e-300)
+        assert np.abs(F - F_ref).max() <= 1e-12 * scale + 1e-300, (name, lj.config_name(cfg))
+        assert abs(U - U_ref) <= 1e-12 * max(abs(U_ref), 1e-300), (name, lj.config_name(cfg))
+        assert d.counters()[1] == np_ref
+    d.close()
+
+
+def test_quantization_matches_oracle(lj):
+    rng = np.random.default_rng(5)
+    L = 12.345
+    x = rng.uniform(-3 * L, 4 * L, size=(3, 5000))
+    x[:, :4] = [[0.0, L, -L, L * (1 - 1e-17)]] * 3
+    d = lj.Domain(L, 2.5, 0.3)
+    d.set_particles(x)
+    pos, _ = d.state()
+    ref = np.array([[oracle.quantize(v, L) for v in row] for row in x], dtype=np.uint32)
+    assert np.array_equal(pos, ref)
+    d.close()
+
+
+def test_integrator_matches_oracle_fp64(lj):
+    s = W.stratified(3000, 0.7, 12, T=1.0)
+    cfg = lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, 8)
+    d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
+    d.set_particles(s.pos, s.vel)
+    d.integrate(0.002, 20, cfg)
+    pos, vel = d.state()
+    p_ref, v_ref, F_ref, _, _ = oracle.vv_run(s.pos, s.vel, s.L, s.rc, 1.0, 0.002, 20, use_cells=True)
+    dp = np.abs(pos.astype(np.int64) - p_ref.astype(np.int64))
+    dp = np.minimum(dp, 2 ** 32 - dp)
+    assert dp.max() <= 2, dp.max()                  # FP64 summation order differs at 1e-16
+    assert np.abs(vel - v_ref).max() <= 1e-9 * np.abs(v_ref).max()
+    assert rel_err(d.forces(), F_ref) <= 1e-8
+    d.close()
+
+
+@pytest.mark.parametrize("cfg_args", [(1, 5, 0, 0), (1, 3, 8, 1), (0, 0, 0, 1), (1, 5, 0, 2)])
+def test_md_run_fp32_vs_fp64_library(lj, cfg_args):
+    """100 steps with Verlet rebuilds every 10 (and the skin check) on FP32 and
+    FP64 paths stay close; the final FP32 forces match the oracle on the final state."""
+    s = W.stratified(8000, 0.75, 21, T=1.0)
+    cfg = lj.config(*cfg_args)
+    d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP32_ACC64)
+    d.set_particles(s.pos, s.vel)
+    d.integrate(0.002, 100, cfg, rebuild_every=10)
+    pos, vel = d.state()
+    cnt = d.counters()
+    assert cnt[2] >= (10 if cfg.container == lj.LJ_VL else 0)
+    d.compute_forces(cfg)
+    F_ref, _, _, _ = oracle.forces_bruteforce(pos, s.L, s.rc)
+    assert rel_err(d.forces(), F_ref) <= 1e-5
+    d.close()
+
+
+def test_newton3_two_pass_is_deterministic(lj, sys_small):
+    s = sys_small
+    cfg = lj.config(lj.LJ_VL, lj.LJ_ORD_VL_IPT, 0, lj.LJ_N3_TWOPASS)
+    outs = []
+    for _ in range(2):
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos, s.vel)
+        d.compute_forces(cfg)
+        outs.append(d.forces())
+        d.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_features_match_oracle(lj):
+    for s in [W.stratified(20000, 0.75, 3), W.slab(20000, 0.8, 0.02, 0.4, 4)]:
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos)
+        f = d.features()
+        ref = oracle.features(s.pos, s.L, s.rc, s.skin)
+        np.testing.assert_allclose(f, ref, rtol=1e-12, atol=1e-14)
+        d.close()
+
+
+def test_mlp_forward_and_gradient_match_oracle(lj):
+    Cn = 33
+    rng = np.random.default_rng(2)
+    P = oracle.mlp_nparams(Cn)
+    p = rng.normal(0, 0.2, size=P)
+    X = rng.normal(size=(200, 16))
+    T = rng.normal(size=(200, Cn))
+    M = (rng.random((200, Cn)) > 0.2).astype(np.float64)
+    Y = lj.mlp_forward(p, Cn, X)
+    np.testing.assert_allclose(Y, oracle.mlp_forward(p.astype(np.float32).astype(np.float64), Cn,
+                                                     X.astype(np.float32).astype(np.float64)), rtol=1e-4, atol=1e-5)
+    loss, g = lj.mlp_loss_grad(p, Cn, X, T, M)
+    p32 = p.astype(np.float32).astype(np.float64)
+    loss_ref, g_ref = oracle.mlp_loss_grad(p32, Cn, X.astype(np.float32).astype(np.float64),
+                                           T.astype(np.float32).astype(np.float64), M)
+    assert loss == pytest.approx(loss_ref, rel=1e-4)
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+
+
+def test_mlp_training_reduces_loss(lj):
+    rng = np.random.default_rng(9)
+    Cn = 8
+    X = rng.normal(size=(256, 16))
+    Wt = rng.normal(size=(16, Cn))
+    T = np.tanh(X @ Wt * 0.3)
+    M = np.ones_like(T)
+    p0 = rng.normal(0, 0.1, size=lj.mlp_nparams(Cn))
+    p, losses = lj.mlp_train(p0, Cn, X, T, M, epochs=500, lr=3e-3)
+    assert losses[-1] < 0.1 * losses[0]
+    # the GPU training follows the oracle's Adam on the same gradients for a few steps
+    q = p0.astype(np.float32).astype(np.float64)
+    m, v = np.zeros_like(q), np.zeros_like(q)
+    X64, T64 = X.astype(np.float32).astype(np.float64), T.astype(np.float32).astype(np.float64)
+    for t in range(1, 4):
+        _, g = oracle.mlp_loss_grad(q, Cn, X64, T64, M)
+        oracle.adam_step(q, g, m, v, 3e-3, t)
+    p3, _ = lj.mlp_train(p0, Cn, X, T, M, epochs=3, lr=3e-3)
+    assert np.abs(p3 - q).max() <= 1e-4
+
+
+def test_capacity_regrowth_and_skin_rebuild(lj):
+    s = W.fcc(4000, 1.2, 5)                       # dense: lists longer than the initial estimate
+    d = lj.Domain(s.L, s.rc, 0.6)
+    d.set_particles(s.pos, s.vel)
+    d.build_verlet(0)
+    assert np.array_equal(d.pairs(lj.LJ_VL), oracle.pairs_bruteforce(s.pos, s.L, s.rc + 0.6))
+    d.close()
+    # a particle teleported by more than skin/2 triggers an early rebuild; FP64
+    # so that a single missed pair (|F| >= |F(r_c)| = 0.039) would stand out
+    s = W.stratified(3000, 0.6, 6)
+    cfg = lj.config(lj.LJ_VL, lj.LJ_ORD_VL_IPT)
+    d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
+    d.set_particles(s.pos, s.vel)
+    d.compute_forces(cfg)
+    builds = d.counters()[2]
+    pos, vel = d.state()
+    vel[:, 0] = [2000.0, 0.0, 0.0]                # moves 4 sigma in one step of dt = 0.002
+    d2 = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
+    d2.set_particles(pos, vel)
+    d2.integrate(0.002, 3, cfg, rebuild_every=1000)
+    assert d2.counters()[3] >= 1                  # early (skin) rebuild counted
+    p2, _ = d2.state()
+    d2.compute_forces(cfg)
+    F_ref, _, _, _ = oracle.forces_bruteforce(p2, s.L, s.rc)
+    assert rel_err(d2.forces(), F_ref) <= 1e-12
+    d.close()
+    d2.close()
+    assert builds >= 1
+
+
+def test_nonfinite_force_is_reported(lj):
+    pos = np.array([[0, 1, 2 ** 31], [0, 0, 0], [0, 0, 0]], dtype=np.uint32)  # two particles 1 unit apart
+    d = lj.Domain(10.0, 2.5, 0.3, precision=lj.LJ_PREC_FP32_ACC64)
+    d.set_particles(pos)
+    with pytest.raises(lj.LJError, match="NONFINITE"):
+        d.compute_forces(lj.config(lj.LJ_LC, lj.LJ_ORD_IPT_SMEM), energy=True)
+    d.close()
+
+
+def test_state_errors(lj):
+    d = lj.Domain(10.0, 2.5, 0.3)
+    with pytest.raises(lj.LJError, match="STATE"):
+        d.compute_forces(lj.config(lj.LJ_LC, lj.LJ_ORD_IPT_SMEM))
+    d.set_particles(np.zeros((3, 4), dtype=np.uint32) + np.arange(4, dtype=np.uint32) * 2 ** 28)
+    with pytest.raises(lj.LJError, match="ARG"):
+        d.compute_forces(lj.config(lj.LJ_LC, lj.LJ_ORD_KI, 3))
+    d.close()
+    small = lj.Domain(5.5, 1.0, 1.0)        # 5 cells for LC, 2 for VL
+    small.set_particles(np.zeros((3, 4), dtype=np.uint32) + np.arange(4, dtype=np.uint32) * 2 ** 28)
+    with pytest.raises(lj.LJError, match="ARG"):
+        small.compute_forces(lj.config(lj.LJ_VL, lj.LJ_ORD_VL_IPT))
+    small.close()
