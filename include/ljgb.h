@@ -247,6 +247,35 @@ lj_status lj_timing(lj_ctx* ctx, int32_t enable, double* force_ms, int64_t* laun
 /* Kinetic energy 1/2 m sum v^2 of the current state (host out). */
 lj_status lj_kinetic_energy(lj_ctx* ctx, double* ke);
 
+/* Allocation-free stable counting sort by cell id, for callers that cannot
+ * allocate device memory when they need cell lists: code running while
+ * another allocator owns the device's memory pool, real-time loops where the
+ * implicit synchronisation of cudaMalloc is not allowed, or programs that must
+ * not fail on allocation after start-up.  The paper has no counterpart; this
+ * is the binning of lj_bin_cells without a context and without allocation.
+ *
+ * pos_fp: device array of 3*n uint32 fixed-point coordinates (SoA), in the
+ * caller's order.  nc: cells per axis (cell of a coordinate = (x * nc) >> 32).
+ * Outputs (device, caller-owned): perm[n] = original index of the k-th
+ * particle in cell order (ties keep ascending original index) and
+ * cell_start[nc^3 + 1].  Work is queued on cuda_stream (NULL = legacy default
+ * stream); the call does not synchronise.
+ *
+ * Scratch lives in one fixed device array inside the library, sized for
+ * n <= LJ_STATIC_MAX_N particles and nc^3 <= LJ_STATIC_MAX_CELLS cells (about
+ * 1.7 MB, held by every GPU that loads the library until the process exits);
+ * larger inputs return LJ_ERR_ARG.  No cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on each device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (other streams or threads) race and must be serialised by the
+ * caller.  Errors: LJ_ERR_ARG (null pointer, n < 1, nc < 1, sizes above the
+ * maxima), LJ_ERR_CUDA. */
+#define LJ_STATIC_MAX_N 65536
+#define LJ_STATIC_MAX_CELLS 32768
+lj_status lj_bin_cells_static(const uint32_t* pos_fp, int64_t n, int32_t nc, uint32_t* perm,
+                              uint32_t* cell_start, void* cuda_stream);
+
 /* Message of the last error on this context (never NULL). */
 const char* lj_last_error(const lj_ctx* ctx);
 

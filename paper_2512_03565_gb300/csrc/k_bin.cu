@@ -6,6 +6,8 @@
 // unique (ties keep ascending original index) and independent of the order of
 // the atomics.  All particle state is then permuted into cell order, which is
 // the order every force kernel reads (structure of arrays, Sec. 2.3.1).
+#include <mutex>
+
 #include "ljgb_internal.cuh"
 
 namespace ljgb {
@@ -342,3 +344,109 @@ cudaError_t build_tiles(Ctx& c, int T) {
 }
 
 }  // namespace ljgb
+
+// ---------------------------------------------------------------------------
+// Allocation-free binning entry point (lj_bin_cells_static).
+//
+// Some callers cannot allocate device memory at the moment they need cell
+// lists: code that runs while another allocator owns the whole device pool
+// (a framework's caching allocator sized to the card), real-time loops where
+// a cudaMalloc's implicit synchronisation is not allowed, or host code that
+// must not fail on allocation after start-up.  This variant of the binning
+// kernels takes device inputs and outputs from the caller and keeps its own
+// scratch (per-cell counters, per-particle cell ids and slots, sort keys and
+// the scan's block totals) in the file-scope device array below, sized for at
+// most LJ_STATIC_MAX_N particles and LJ_STATIC_MAX_CELLS cells.  Every GPU that
+// loads the library holds this array until the process exits.
+// ---------------------------------------------------------------------------
+namespace ljgb {
+namespace {
+
+constexpr int64_t kStaticMaxN = 65536;       // LJ_STATIC_MAX_N
+constexpr int64_t kStaticMaxCells = 32768;   // LJ_STATIC_MAX_CELLS (n_c <= 32)
+constexpr int64_t kStaticScanBlocks = (kStaticMaxCells + SCAN_TILE - 1) / SCAN_TILE + 1;
+// byte offsets of the scratch regions (each 256-byte aligned)
+constexpr size_t kOffCnt = 0;
+constexpr size_t kOffCellOf = kOffCnt + 256 * ((4 * (kStaticMaxCells + 1) + 255) / 256);
+constexpr size_t kOffSlot = kOffCellOf + 4 * kStaticMaxN;
+constexpr size_t kOffKey = kOffSlot + 4 * kStaticMaxN;
+constexpr size_t kOffKey2 = kOffKey + 8 * kStaticMaxN;
+constexpr size_t kOffScan = kOffKey2 + 8 * kStaticMaxN;
+constexpr size_t kStaticBytes = kOffScan + 256 * ((4 * kStaticScanBlocks + 255) / 256);
+
+static __device__ __align__(256) unsigned char g_bin_scratch[kStaticBytes];
+
+// Device address of g_bin_scratch per device, looked up once per device with
+// that device current.  In host code the symbol g_bin_scratch is only a
+// host-side stand-in and must never be passed to a kernel.
+std::mutex g_scratch_mu;
+void* g_scratch_addr[128] = {nullptr};
+
+cudaError_t static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_bin_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+__global__ void k_cell_ids_soa(const uint32_t* __restrict__ pos, int64_t n, uint32_t nc, uint32_t* __restrict__ cell_of,
+                               uint32_t* __restrict__ slot, uint32_t* __restrict__ cnt) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t c = (cell_coord(pos[2 * n + s], nc) * nc + cell_coord(pos[n + s], nc)) * nc + cell_coord(pos[s], nc);
+  cell_of[s] = c;
+  slot[s] = atomicAdd(&cnt[c], 1u);
+}
+
+__global__ void k_scatter_keys_soa(int64_t n, const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ slot,
+                                   const uint32_t* __restrict__ cell_start, unsigned long long* __restrict__ key) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  key[cell_start[cell_of[s]] + slot[s]] = (unsigned long long)s << 32;
+}
+
+__global__ void k_keys_to_perm(const unsigned long long* __restrict__ key, int64_t n, uint32_t* __restrict__ perm) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) perm[k] = (uint32_t)(key[k] >> 32);
+}
+
+}  // namespace
+}  // namespace ljgb
+
+extern "C" lj_status lj_bin_cells_static(const uint32_t* pos_fp, int64_t n, int32_t nc, uint32_t* perm,
+                                         uint32_t* cell_start, void* cuda_stream) {
+  using namespace ljgb;
+  if (!pos_fp || !perm || !cell_start || n < 1 || n > kStaticMaxN || nc < 1) return LJ_ERR_ARG;
+  const int64_t ncell = (int64_t)nc * nc * nc;
+  if (ncell > kStaticMaxCells) return LJ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  void* base = nullptr;
+  if (static_scratch(&base) != cudaSuccess) return LJ_ERR_CUDA;
+  unsigned char* b = (unsigned char*)base;
+  uint32_t* cnt = (uint32_t*)(b + kOffCnt);
+  uint32_t* cell_of = (uint32_t*)(b + kOffCellOf);
+  uint32_t* slot = (uint32_t*)(b + kOffSlot);
+  unsigned long long* key = (unsigned long long*)(b + kOffKey);
+  unsigned long long* key2 = (unsigned long long*)(b + kOffKey2);
+  uint32_t* scan_tot = (uint32_t*)(b + kOffScan);
+  // the counters keep the previous call's values: clear them first
+  if (cudaMemsetAsync(cnt, 0, (size_t)ncell * sizeof(uint32_t), s) != cudaSuccess) return LJ_ERR_CUDA;
+  k_cell_ids_soa<<<nblk(n, 256), 256, 0, s>>>(pos_fp, n, (uint32_t)nc, cell_of, slot, cnt);
+  const int64_t nb = (ncell + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<(unsigned)nb, SCAN_T, 0, s>>>(cnt, cell_start, ncell, scan_tot);
+  k_scan_totals<<<1, SCAN_T, 0, s>>>(scan_tot, nb, cell_start + ncell);
+  k_scan_add<<<(unsigned)nb, SCAN_T, 0, s>>>(cell_start, ncell, scan_tot);
+  k_scatter_keys_soa<<<nblk(n, 256), 256, 0, s>>>(n, cell_of, slot, cell_start, key);
+  k_sort_cells<<<nblk(ncell * 32, 256), 256, 0, s>>>(cell_start, ncell, key, key2);
+  k_keys_to_perm<<<nblk(n, 256), 256, 0, s>>>(key2, n, perm);
+  return cudaGetLastError() == cudaSuccess ? LJ_OK : LJ_ERR_CUDA;
+}

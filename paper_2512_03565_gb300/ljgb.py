@@ -90,6 +90,7 @@ _SIGS = {
     "lj_get_counters": (C.c_int, [_VP, _VP]),
     "lj_kinetic_energy": (C.c_int, [_VP, C.POINTER(C.c_double)]),
     "lj_timing": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP]),
+    "lj_bin_cells_static": (C.c_int, [_VP, C.c_int64, C.c_int32, _VP, _VP, _VP]),
     "lj_last_error": (C.c_char_p, [_VP]),
     "lj_destroy": (None, [_VP]),
 }
