@@ -247,6 +247,45 @@ lj_status lj_timing(lj_ctx* ctx, int32_t enable, double* force_ms, int64_t* laun
 /* Kinetic energy 1/2 m sum v^2 of the current state (host out). */
 lj_status lj_kinetic_energy(lj_ctx* ctx, double* ke);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent periodic boxes of uneven sizes advanced together
+ * by one persistent kernel launch (cooperative, all blocks resident), captured
+ * as a CUDA graph and replayed.  Each box runs velocity Verlet (Sec. 2.1) with
+ * linked-cell forces (Sec. 2.1.1; cells of edge >= cutoff rebinned every
+ * step, boxes with fewer than 3 cells per axis use all pairs) in the JSPLIT<w>
+ * order (Sec. 4.1), FP32 pair math and FP64 accumulation.  The phases of a
+ * step are separated by a grid barrier whose waits are bounded: a wait that
+ * gives up ends the launch and the run returns LJ_ERR_TIMEOUT.
+ * ------------------------------------------------------------------------ */
+typedef struct lj_ens lj_ens;
+
+/* nboxes boxes; box b has edge box_L[b] (> 2 cutoff) and counts[b] particles.
+ * pos_fp / vel (host): per box 3*n_b entries (SoA) at offset 3*off_b, off_b =
+ * sum of the counts before b; vel may be NULL.  cuda_stream may be NULL (the
+ * ensemble then uses a stream of its own).  Errors: LJ_ERR_ARG, LJ_ERR_OOM,
+ * LJ_ERR_CUDA. */
+lj_status lj_ensemble_create(lj_ens** out, int32_t nboxes, const double* box_L, const int64_t* counts,
+                             const uint32_t* pos_fp, const double* vel, double cutoff, double eps, double sigma,
+                             double mass, void* cuda_stream);
+/* nsteps steps of every box in one launch (initial forces first if none are
+ * current); use_graph = 1 captures the launch as a CUDA graph and replays it.
+ * Synchronises.  Errors: LJ_ERR_ARG, LJ_ERR_TIMEOUT, LJ_ERR_NONFINITE, LJ_ERR_CUDA. */
+lj_status lj_ensemble_run(lj_ens* ens, double dt, int32_t nsteps, int32_t use_graph);
+/* Autotunes the launch shape (JSPLIT width w in {2,4,8,16}, block size in
+ * {128,256,512}) by timing `steps` steps of each on a copy of the state. */
+lj_status lj_ensemble_tune(lj_ens* ens, double dt, int32_t steps, int32_t* w_out, int32_t* block_out);
+/* Copies the state out in the caller's layout and order (any pointer may be NULL). */
+lj_status lj_ensemble_get(lj_ens* ens, uint32_t* pos_fp, double* vel, double* frc);
+/* Failure-path test hook: barrier spin bound (0 = default, about seconds) and
+ * a block that leaves before its first barrier (-1 = none). */
+lj_status lj_ensemble_debug(lj_ens* ens, uint32_t spin_limit, int32_t skip_block);
+int64_t lj_ensemble_size(const lj_ens* ens);
+/* Message of the last ensemble error or fallback (never NULL). */
+const char* lj_ensemble_last_error(const lj_ens* ens);
+/* 1 if the last run replayed a captured CUDA graph. */
+int32_t lj_ensemble_uses_graph(const lj_ens* ens);
+void lj_ensemble_destroy(lj_ens* ens);
+
 /* Allocation-free stable counting sort by cell id, for callers that cannot
  * allocate device memory when they need cell lists: code running while
  * another allocator owns the device's memory pool, real-time loops where the

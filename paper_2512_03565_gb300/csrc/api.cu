@@ -9,6 +9,7 @@
 // fastest by the mean of its samples.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 
@@ -226,6 +227,19 @@ lj_status do_build_verlet(Ctx& c, int half, int colmajor, bool twopass) {
   }
   c.vl_half = half;
   c.vl_colmajor = colmajor;
+  // 16-bit copy of the lists (halves the list bytes) when every entry
+  // j - i, wrapped modulo n, is guaranteed to fit: n <= 65536.  In larger
+  // boxes the neighbours across the periodic faces in y and x lie up to a
+  // full z-layer of cells away in cell order.
+  c.vl_idx16 = false;
+  if (!twopass && c.n <= 65536) {
+    CK(launch_list_to16(c, c.maxlen));
+    c.launches += 1;
+    uint32_t ovf = 1;
+    CK(cudaMemcpyAsync(&ovf, c.maxlen, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    c.vl_idx16 = ovf == 0;
+  }
   c.vl_valid = true;
   c.rev_valid = false;
   c.steps_since_build = 0;
@@ -332,8 +346,10 @@ lj_status run_force(Ctx& c, const lj_config& cfg, bool ev) {
   if (t1) CK(cudaEventRecord(t1, c.stream));
   CK(e);
   c.launches += force_launches(c, cfg, c.tiles_gen != tiles_before || c.tiles_T != tiles_T_before);
-  CK(launch_check_finite(c));
-  c.launches += 1;
+  if (!(cfg.container == LJ_VL && cfg.newton3 == LJ_N3_OFF)) {  // fused into the VL N3-off store
+    CK(launch_check_finite(c));
+    c.launches += 1;
+  }
   c.forces_valid = true;
   c.counters[0] += 1;
   return LJ_OK;
@@ -395,11 +411,8 @@ lj_status lj_init_domain(lj_ctx** out, const double box[3], double cutoff, doubl
   LJParams& P = c.P;
   P.Rc2 = exact_cut2(L, cutoff);
   c.Rl2 = exact_cut2(L, cutoff + skin);
-  const double R2 = (double)P.Rc2;
-  P.rc2f_lo = std::nextafter((float)(R2 * (1.0 - 1e-6)), 0.0f);
-  P.rc2f_hi = std::nextafter((float)(R2 * (1.0 + 1e-6)), std::numeric_limits<float>::infinity());
-  P.rc2d_lo = R2 * (1.0 - 1e-13);
-  P.rc2d_hi = R2 * (1.0 + 1e-13);
+  coarse_band(P.Rc2, &P.rc2p_lo, &P.rc2p_hi);
+  coarse_band(c.Rl2, &c.rl2p_lo, &c.rl2p_hi);
   P.S = (sigma * sigma) / (u * u);
   P.S_hi = (float)P.S;
   P.S_lo = (float)(P.S - (double)P.S_hi);
@@ -418,6 +431,24 @@ lj_status lj_init_domain(lj_ctx** out, const double box[3], double cutoff, doubl
   if (e == cudaSuccess) e = cudaMallocHost(&c.host_status, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(c.status, 0, sizeof(uint32_t), c.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e == cudaSuccess) {
+    // L2 set-aside for persisting accesses (this process's context only): the
+    // Verlet-list kernels keep the gathered positions resident with it.
+    // LJGB_L2_PERSIST_MB=0 disables it.
+    int dev = 0, maxwin = 0, maxpers = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxwin, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    cudaDeviceGetAttribute(&maxpers, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    const char* env = std::getenv("LJGB_L2_PERSIST_MB");
+    size_t want = (size_t)(env ? std::atoi(env) : 48) << 20;
+    want = std::min(want, (size_t)std::min(maxwin, maxpers));
+    size_t cur = 0;
+    if (want > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
+      if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) want = 0;
+      c.l2_window_bytes = want;
+    }
+    cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     lj_destroy(h);
     return e == cudaErrorMemoryAllocation ? LJ_ERR_OOM : LJ_ERR_CUDA;
@@ -789,7 +820,7 @@ void lj_destroy(lj_ctx* h) {
   void* dev[] = {c.pos, c.pos_alt, c.vel, c.vel_alt, c.frc, c.frc_alt, c.cell_start, c.cnt, c.cell_of, c.slot,
                  c.key, c.scan_tmp, c.tiles, c.row_tiles, c.nbr, c.nnbr, c.x_build, c.maxlen, c.twopass,
                  c.rev_cnt, c.rev_start, c.rev_slot, c.rev_key, c.rev_key2, c.ev, c.npairs, c.status,
-                 c.feat_stats, c.tile_ctr, c.stage};
+                 c.feat_stats, c.tile_ctr, c.stage, c.nbr16};
   for (void* p : dev) dfree(p);
   if (c.host_ev) cudaFreeHost(c.host_ev);
   if (c.host_np) cudaFreeHost(c.host_np);

@@ -80,25 +80,53 @@ cudaError_t force_lc_t(Ctx& c, const lj_config& cfg, bool ev) {
   return ev ? lc_launch<R, false, true>(c, cfg, out) : lc_launch<R, false, false>(c, cfg, out);
 }
 
-template <typename R, int N3, bool EV>
-cudaError_t vl_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
-  VLArgs A{c.pos, c.nbr, c.nnbr, c.vl_cap, c.twopass};
+// Launch of a Verlet-list kernel with an L2 access-policy window over the
+// position array: the positions (16 B per particle, gathered ~70 times each)
+// persist in L2 while the list entries (read once) stream past them.
+template <typename... KArgs, typename... Args>
+cudaError_t vl_launch_ex(const Ctx& c, void (*k)(KArgs...), unsigned grid, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = c.stream;
+  cudaLaunchAttribute attr[1];
+  unsigned na = 0;
+  if (c.l2_window_bytes > 0) {
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = (void*)c.pos;
+    attr[0].val.accessPolicyWindow.num_bytes = std::min(c.l2_window_bytes, (size_t)c.n * sizeof(uint4));
+    attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    na = 1;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <typename R, int N3, bool EV, bool I16>
+cudaError_t vl_launch_i(Ctx& c, const lj_config& cfg, ForceOut out) {
+  VLArgs A{c.pos, c.nbr, I16 ? c.nbr16 : nullptr, c.nnbr, c.vl_cap, c.twopass, c.status};
   const int64_t n = c.n;
   if (cfg.order == LJ_ORD_VL_IPT) {
-    k_vl_ipt<R, N3, EV><<<grid_for(n, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
+    return vl_launch_ex(c, k_vl_ipt<R, N3, EV, I16>, grid_for(n, 256, 8), c.P, A, out);
   } else if (N3 != 2) {
-    const int64_t thr = n * cfg.param;
+    const unsigned g = grid_for(n * cfg.param, 256, 16);
     switch (cfg.param) {
-      case 32: k_vl_jsplit<R, 32, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, A, out); break;
-      case 16: k_vl_jsplit<R, 16, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, A, out); break;
-      case 8: k_vl_jsplit<R, 8, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, A, out); break;
-      case 4: k_vl_jsplit<R, 4, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, A, out); break;
-      default: k_vl_jsplit<R, 2, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, A, out); break;
+      case 32: return vl_launch_ex(c, k_vl_jsplit<R, 32, N3, EV, I16>, g, c.P, A, out);
+      case 16: return vl_launch_ex(c, k_vl_jsplit<R, 16, N3, EV, I16>, g, c.P, A, out);
+      case 8: return vl_launch_ex(c, k_vl_jsplit<R, 8, N3, EV, I16>, g, c.P, A, out);
+      case 4: return vl_launch_ex(c, k_vl_jsplit<R, 4, N3, EV, I16>, g, c.P, A, out);
+      default: return vl_launch_ex(c, k_vl_jsplit<R, 2, N3, EV, I16>, g, c.P, A, out);
     }
-  } else {
-    return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, int N3, bool EV>
+cudaError_t vl_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
+  return c.vl_idx16 ? vl_launch_i<R, N3, EV, true>(c, cfg, out) : vl_launch_i<R, N3, EV, false>(c, cfg, out);
 }
 
 template <typename R>

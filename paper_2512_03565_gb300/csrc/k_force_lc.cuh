@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
           for (int k = 0; k < K; ++k) {
             if (vi[k] && seg_ok(sg.kind, jidx, ii[k], cxi[k], nc)) {
               R af, bf, cf_;
-              const R fac = Prec<R>::template pair<EV>(mimg(pi[k].x, pj.x), mimg(pi[k].y, pj.y),
+              const R fac = Prec<R>::template pair<EV, true>(mimg(pi[k].x, pj.x), mimg(pi[k].y, pj.y),
                                                        mimg(pi[k].z, pj.z), P, af, bf, cf_, eu, ew, cnt);
               fx[k] += fac * af;
               fy[k] += fac * bf;
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
         R hx = 0, hy = 0, hz = 0;
         if (vi && seg_ok(sg.kind, jidx, ii, cxi, nc)) {
           R af, bf, cf_;
-          const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af,
+          const R fac = Prec<R>::template pair<EV, true>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af,
                                                    bf, cf_, eu, ew, cnt);
           fx += fac * af;
           fy += fac * bf;
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
           const uint32_t src = (uint32_t)((lane + r) & 31);
           if (vi && src < m && seg_ok(sg.kind, jb + src, ii, cxi, nc)) {
             R af, bf, cf_;
-            const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P,
+            const R fac = Prec<R>::template pair<EV, true>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P,
                                                      af, bf, cf_, eu, ew, cnt);
             fx += fac * af;
             fy += fac * bf;
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
         if (j < sg.e && seg_ok(sg.kind, j, ii, (uint32_t)cx, nc)) {
           const uint4 pj = pos[j];
           R af, bf, cf_;
-          const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af,
+          const R fac = Prec<R>::template pair<EV, true>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af,
                                                    bf, cf_, eu, ew, cnt);
           fx += fac * af;
           fy += fac * bf;

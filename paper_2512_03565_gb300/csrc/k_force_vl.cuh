@@ -20,18 +20,49 @@ namespace ljgb {
 struct VLArgs {
   const uint4* pos;
   const int32_t* nbr;
+  const int16_t* nbr16;  // 16-bit entries (j - i wrapped modulo n), same layout; used when non-null
   const int32_t* nnbr;
   int cap;
   void* slot;      // two-pass: per-entry j contributions, R[3][cap * n] (column-major slots)
+  uint32_t* status;
 };
+
+// Entry k of a list: the 32-bit index, or i plus the 16-bit wrapped
+// difference.  List entries are read once per evaluation: streaming loads keep
+// them from displacing the positions in L2.
+template <bool I16>
+__device__ __forceinline__ int vl_entry(const VLArgs& A, int64_t e, int64_t i, int64_t n) {
+  if (I16) {
+    int64_t j = i + (int64_t)__ldcs(A.nbr16 + e);
+    j += (j < 0) ? n : 0;
+    j -= (j >= n) ? n : 0;
+    return (int)j;
+  }
+  return __ldcs(A.nbr + e);
+}
+
+// Stores the FP64 force of particle i; a non-finite result sets ST_NONFINITE.
+__device__ __forceinline__ void vl_store(const ForceOut& out, uint32_t* status, int64_t i, double f0, double f1,
+                                         double f2) {
+  out.fx[i] = f0;
+  out.fy[i] = f1;
+  out.fz[i] = f2;
+  if (!isfinite(f0 + f1 + f2)) atomicOr(status, ST_NONFINITE);
+}
 
 template <typename R>
 __device__ __forceinline__ void vl_atomic(double* p, R v, double scale) {
   if (v != (R)0) atomicAdd(p, scale * Prec<R>::to_d(v));
 }
 
+// Entries are processed in batches of VL_BATCH: the batch's list entries are
+// loaded, then its positions gathered, then its pairs computed, so that every
+// lane keeps several independent gathers in flight.  A short last batch is
+// padded with j = i, which the exact R^2 = 0 rule rejects.
+constexpr int VL_BATCH = 4;
+
 // N3: 0 = off, 1 = atomic, 2 = two-pass (pass 1)
-template <typename R, int N3, bool EV>
+template <typename R, int N3, bool EV, bool I16>
 __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut out) {
   const int64_t n = P.n;
   double eu_d = 0.0, ew_d = 0.0;
@@ -43,27 +74,36 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
     if (vi) {
       const uint4 pi = A.pos[i];
       const int m = min(A.nnbr[i], A.cap);
-#pragma unroll 2
-      for (int k = 0; k < m; ++k) {
-        const int j = A.nbr[(int64_t)k * n + i];
-        const uint4 pj = A.pos[j];
-        R af, bf, cf;
-        const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af, bf,
-                                                 cf, eu, ew, cnt);
-        fx += fac * af;
-        fy += fac * bf;
-        fz += fac * cf;
-        if (N3 == 1) {
-          vl_atomic(out.fx + j, fac * af, P.e24u);
-          vl_atomic(out.fy + j, fac * bf, P.e24u);
-          vl_atomic(out.fz + j, fac * cf, P.e24u);
-        } else if (N3 == 2) {
-          const int64_t e = (int64_t)k * n + i;
-          const int64_t ne = (int64_t)A.cap * n;
-          R* sl = (R*)A.slot;
-          sl[e] = fac * af;
-          sl[ne + e] = fac * bf;
-          sl[2 * ne + e] = fac * cf;
+      for (int k0 = 0; k0 < m; k0 += VL_BATCH) {
+        int jj[VL_BATCH];
+        uint4 pj[VL_BATCH];
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t)
+          jj[t] = (k0 + t < m) ? vl_entry<I16>(A, (int64_t)(k0 + t) * n + i, i, n) : (int)i;
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jj[t]);
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t) {
+          R af, bf, cf;
+          const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj[t].x), mimg(pi.y, pj[t].y), mimg(pi.z, pj[t].z), P,
+                                                   af, bf, cf, eu, ew, cnt);
+          fx += fac * af;
+          fy += fac * bf;
+          fz += fac * cf;
+          if (N3 == 1) {
+            vl_atomic(out.fx + jj[t], fac * af, P.e24u);
+            vl_atomic(out.fy + jj[t], fac * bf, P.e24u);
+            vl_atomic(out.fz + jj[t], fac * cf, P.e24u);
+          } else if (N3 == 2) {
+            if (k0 + t < m) {
+              const int64_t e = (int64_t)(k0 + t) * n + i;
+              const int64_t ne = (int64_t)A.cap * n;
+              R* sl = (R*)A.slot;
+              sl[e] = fac * af;
+              sl[ne + e] = fac * bf;
+              sl[2 * ne + e] = fac * cf;
+            }
+          }
         }
       }
       if (N3 == 1) {
@@ -71,9 +111,8 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
         vl_atomic(out.fy + i, fy, -P.e24u);
         vl_atomic(out.fz + i, fz, -P.e24u);
       } else {
-        out.fx[i] = -P.e24u * Prec<R>::to_d(fx);
-        out.fy[i] = -P.e24u * Prec<R>::to_d(fy);
-        out.fz[i] = -P.e24u * Prec<R>::to_d(fz);
+        vl_store(out, A.status, i, -P.e24u * Prec<R>::to_d(fx), -P.e24u * Prec<R>::to_d(fy),
+                 -P.e24u * Prec<R>::to_d(fz));
       }
     }
     if (EV) {
@@ -84,7 +123,7 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
   block_flush<R>(eu_d, ew_d, cnt, out, EV);
 }
 
-template <typename R, int W, int N3, bool EV>
+template <typename R, int W, int N3, bool EV, bool I16>
 __global__ void __launch_bounds__(256) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
   constexpr int G = 32 / W;
   const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
@@ -99,20 +138,28 @@ __global__ void __launch_bounds__(256) k_vl_jsplit(LJParams P, VLArgs A, ForceOu
     if (vi) {
       const uint4 pi = A.pos[i];
       const int m = min(A.nnbr[i], A.cap);
-      const int32_t* row = A.nbr + i * A.cap;
-      for (int k = sub; k < m; k += W) {
-        const int j = row[k];
-        const uint4 pj = A.pos[j];
-        R af, bf, cf;
-        const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af, bf,
-                                                 cf, eu, ew, cnt);
-        fx += fac * af;
-        fy += fac * bf;
-        fz += fac * cf;
-        if (N3 == 1) {
-          vl_atomic(out.fx + j, fac * af, P.e24u);
-          vl_atomic(out.fy + j, fac * bf, P.e24u);
-          vl_atomic(out.fz + j, fac * cf, P.e24u);
+      const int64_t row = i * A.cap;
+      for (int k0 = sub; k0 < m; k0 += W * VL_BATCH) {
+        int jj[VL_BATCH];
+        uint4 pj[VL_BATCH];
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t)
+          jj[t] = (k0 + t * W < m) ? vl_entry<I16>(A, row + k0 + t * W, i, n) : (int)i;
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jj[t]);
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t) {
+          R af, bf, cf;
+          const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj[t].x), mimg(pi.y, pj[t].y), mimg(pi.z, pj[t].z), P,
+                                                   af, bf, cf, eu, ew, cnt);
+          fx += fac * af;
+          fy += fac * bf;
+          fz += fac * cf;
+          if (N3 == 1) {
+            vl_atomic(out.fx + jj[t], fac * af, P.e24u);
+            vl_atomic(out.fy + jj[t], fac * bf, P.e24u);
+            vl_atomic(out.fz + jj[t], fac * cf, P.e24u);
+          }
         }
       }
     }
@@ -128,9 +175,8 @@ __global__ void __launch_bounds__(256) k_vl_jsplit(LJParams P, VLArgs A, ForceOu
         vl_atomic(out.fy + i, fy, -P.e24u);
         vl_atomic(out.fz + i, fz, -P.e24u);
       } else {
-        out.fx[i] = -P.e24u * Prec<R>::to_d(fx);
-        out.fy[i] = -P.e24u * Prec<R>::to_d(fy);
-        out.fz[i] = -P.e24u * Prec<R>::to_d(fz);
+        vl_store(out, A.status, i, -P.e24u * Prec<R>::to_d(fx), -P.e24u * Prec<R>::to_d(fy),
+                 -P.e24u * Prec<R>::to_d(fz));
       }
     }
     if (EV) {

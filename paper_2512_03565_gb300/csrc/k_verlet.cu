@@ -2,68 +2,92 @@
 // particles within cutoff + skin, built with the help of the linked-cell
 // structure and rebuilt every few steps).
 //
-// One warp per particle i scans the 27 cells of edge >= r_c + skin around its
-// cell (9 rows, each an ascending run of cells) in strides of 32 candidates,
-// keeps j != i with 0 < R^2 <= floor((r_l/u)^2) (half lists: j > i), and
-// compacts the survivors with a warp ballot: each kept lane's slot is the
-// running count plus the number of kept lanes below it, so the list keeps the
-// scan order.  Lists longer than the capacity keep counting, set ST_CAPACITY
-// and report the longest list so the host can regrow and rebuild.
+// The builder walks row tiles (<= 32 consecutive particles of one cell row,
+// the tiles of the linked-cell kernels): a warp loads each 32-particle chunk of
+// the tile's neighbour segments once, then for every i of the tile tests the
+// chunk's 32 j's (one per lane) with the exact integer rule, keeps j != i with
+// 0 < R^2 <= floor((r_l/u)^2) (half lists: j > i), and compacts the survivors
+// with a warp ballot: each kept lane's slot is i's running count plus the
+// number of kept lanes below it.  Every i therefore receives its j's in the
+// scan order of rows (dz, dy) and ascending index, and its entries of one chunk
+// are written as consecutive stores.  The tile's running counts live in lane
+// registers (lane q holds the q-th particle's), and the coarse float screen
+// (coarse_r2) settles every candidate except those in a thin band around r_l,
+// which get the exact 64-bit test.  Lists longer than the capacity keep
+// counting, set ST_CAPACITY and report the longest list so the host can
+// regrow and rebuild.
 #include "k_force_lc.cuh"
 
 namespace ljgb {
 
 __global__ void __launch_bounds__(256) k_build_verlet(const uint4* __restrict__ pos, const uint32_t* __restrict__ cs,
                                                       int nc, int n, uint64_t Rl2, int half, int cap, int colmajor,
-                                                      int32_t* __restrict__ nbr, int32_t* __restrict__ nnbr,
-                                                      uint32_t* __restrict__ xb, uint32_t* __restrict__ maxlen,
-                                                      uint32_t* __restrict__ status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+                                                      const uint4* __restrict__ tiles,
+                                                      const uint32_t* __restrict__ ntiles_ptr,
+                                                      uint32_t* __restrict__ tile_ctr, int32_t* __restrict__ nbr,
+                                                      int32_t* __restrict__ nnbr, uint32_t* __restrict__ xb,
+                                                      uint32_t* __restrict__ maxlen, uint32_t* __restrict__ status,
+                                                      float rl2p_lo, float rl2p_hi) {
+  __shared__ uint4 s_i[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nwarps) {
-    const uint32_t i = (uint32_t)w;
-    const uint4 pi = pos[i];
-    const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
-    uint32_t count = 0;
+  const uint32_t ntiles = *ntiles_ptr;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(tile_ctr, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= ntiles) break;
+    const uint4 tile = tiles[t];
+    const int cf = (int)(tile.w & 0xffffu), cl = (int)(tile.w >> 16);
+    const uint32_t ni = tile.y - tile.x;
+    if (lane < (int)ni) {
+      const uint4 p = pos[tile.x + lane];
+      s_i[wib][lane] = p;
+      xb[tile.x + lane] = p.x;
+      xb[(int64_t)n + tile.x + lane] = p.y;
+      xb[2 * (int64_t)n + tile.x + lane] = p.z;
+    }
+    uint32_t my_cnt = 0;  // lane q counts the list of the tile's q-th particle
+    __syncwarp();
+    Seg segs[18];
+    const int ns = make_segments<false>(cs, nc, (int)tile.z, cf, cl, tile.x, segs);
 #pragma unroll 1
-    for (int dz = -1; dz <= 1; ++dz) {
+    for (int s = 0; s < ns; ++s) {
 #pragma unroll 1
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int r = ((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc;
-        Seg sg[2];
-        const int ns = row_segments(cs, nc, r, cx - 1, cx + 1, sg);
-#pragma unroll 1
-        for (int s = 0; s < ns; ++s) {
-#pragma unroll 1
-          for (uint32_t jb = sg[s].b; jb < sg[s].e; jb += 32) {
-            const uint32_t j = jb + lane;
-            bool in = false;
-            if (j < sg[s].e && j != i && (!half || j > i)) {
-              const uint4 pj = pos[j];
-              in = in_cut_exact(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), Rl2);
+      for (uint32_t jb = segs[s].b; jb < segs[s].e; jb += 32) {
+        const uint32_t j = jb + lane;
+        const bool vj = j < segs[s].e;
+        const uint4 pj = vj ? pos[j] : make_uint4(0, 0, 0, 0);
+#pragma unroll 4
+        for (uint32_t q = 0; q < ni; ++q) {
+          const uint4 pi = s_i[wib][q];
+          const uint32_t i = tile.x + q;
+          const int da = mimg(pi.x, pj.x), db = mimg(pi.y, pj.y), dc = mimg(pi.z, pj.z);
+          const float r2p = coarse_r2(da, db, dc);
+          // coarse screen decides both sides; only the thin band needs the exact test
+          bool in = vj && ((da | db | dc) != 0) && (!half || j > i) && r2p <= rl2p_hi;
+          if (in && r2p >= rl2p_lo) in = in_cut_exact(da, db, dc, Rl2);
+          const unsigned mask = __ballot_sync(0xffffffffu, in);
+          const uint32_t base = __shfl_sync(0xffffffffu, my_cnt, (int)q);
+          if (in) {
+            const uint32_t k = base + __popc(mask & lt);
+            if (k < (uint32_t)cap) {
+              if (colmajor)
+                nbr[(int64_t)k * n + i] = (int32_t)j;
+              else
+                nbr[(int64_t)i * cap + k] = (int32_t)j;
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, in);
-            if (in) {
-              const uint32_t k = count + __popc(mask & lt);
-              if (k < (uint32_t)cap) {
-                if (colmajor)
-                  nbr[(int64_t)k * n + i] = (int32_t)j;
-                else
-                  nbr[(int64_t)i * cap + k] = (int32_t)j;
-              }
-            }
-            count += __popc(mask);
           }
+          if (lane == (int)q) my_cnt += __popc(mask);
         }
       }
     }
-    if (lane == 0) {
-      nnbr[i] = (int32_t)count;
-      if (count > (uint32_t)cap) atomicOr(status, ST_CAPACITY);
-      atomicMax(maxlen, count);
+    if (lane < (int)ni) {
+      nnbr[tile.x + lane] = (int32_t)my_cnt;
+      if (my_cnt > (uint32_t)cap) atomicOr(status, ST_CAPACITY);
+      atomicMax(maxlen, my_cnt);
     }
-    if (lane < 3) xb[(int64_t)lane * n + i] = lane == 0 ? pi.x : (lane == 1 ? pi.y : pi.z);
+    __syncwarp();
   }
 }
 
@@ -114,9 +138,49 @@ static inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t)
 
 cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen) {
   const int64_t n = c.n;
-  const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, 152 * 64);
+  cudaError_t e = build_tiles(c, 32);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c.tile_ctr, 0, sizeof(uint32_t), c.stream)) != cudaSuccess) return e;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8);
   k_build_verlet<<<blocks, 256, 0, c.stream>>>(c.pos, c.cell_start, c.binned_nc, (int)n, c.Rl2, half, c.vl_cap,
-                                                colmajor, c.nbr, c.nnbr, c.x_build, maxlen, c.status);
+                                                colmajor, c.tiles, c.row_tiles + (size_t)c.binned_nc * c.binned_nc,
+                                                c.tile_ctr, c.nbr, c.nnbr, c.x_build, maxlen, c.status, c.rl2p_lo,
+                                                c.rl2p_hi);
+  return cudaGetLastError();
+}
+
+// 16-bit copy of the lists: entry j stored as j - i wrapped into [-n/2, n/2);
+// any entry outside the int16 range sets *overflow (the 32-bit list is used).
+__global__ void k_list_to16(const int32_t* __restrict__ nbr, const int32_t* __restrict__ nnbr, int64_t n, int cap,
+                            int colmajor, int16_t* __restrict__ out, uint32_t* __restrict__ overflow) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)cap * n) return;
+  const int64_t i = colmajor ? e % n : e / cap;
+  const int k = colmajor ? (int)(e / n) : (int)(e % cap);
+  if (k >= min(nnbr[i], cap)) return;
+  int64_t d = (int64_t)nbr[e] - i;
+  if (d >= (n + 1) / 2) d -= n;
+  if (d < -(n / 2)) d += n;
+  if (d < -32768 || d > 32767) {
+    atomicOr(overflow, 1u);
+    return;
+  }
+  out[e] = (int16_t)d;
+}
+
+cudaError_t launch_list_to16(Ctx& c, uint32_t* overflow) {
+  const int64_t ne = (int64_t)c.vl_cap * c.n;
+  if ((size_t)ne > c.nbr16_cap) {
+    if (c.nbr16) cudaFree(c.nbr16);
+    c.nbr16 = nullptr;
+    c.nbr16_cap = 0;
+    cudaError_t e = cudaMalloc(&c.nbr16, (size_t)ne * sizeof(int16_t));
+    if (e != cudaSuccess) return e;
+    c.nbr16_cap = (size_t)ne;
+  }
+  cudaError_t e = cudaMemsetAsync(overflow, 0, sizeof(uint32_t), c.stream);
+  if (e != cudaSuccess) return e;
+  k_list_to16<<<nb(ne, 256), 256, 0, c.stream>>>(c.nbr, c.nnbr, c.n, c.vl_cap, c.vl_colmajor, c.nbr16, overflow);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -38,8 +39,7 @@ struct LJParams {
   int32_t n;          // particles
   int32_t nc;         // cells per axis of the active container
   uint64_t Rc2;       // floor((r_c/u)^2)
-  float rc2f_lo, rc2f_hi;    // FP32 decision band around Rc2 (exact test inside)
-  double rc2d_lo, rc2d_hi;   // FP64 decision band
+  float rc2p_lo, rc2p_hi;  // coarse_r2 thresholds: certainly inside below lo, outside above hi
   float S_hi, S_lo;   // S = sigma^2/u^2 as an unevaluated float sum
   double S;           // S in FP64
   double e24u;        // 24 eps / u
@@ -111,21 +111,52 @@ __device__ __forceinline__ float rcp_nr(float x) {
 // The pair kernel (Algorithm 1's ForceKernel), FP32 and FP64 variants.
 //
 // Input: the fixed-point difference (a,b,c) = x_j - x_i (minimum image).
-// Output: fac' (0 when the pair is outside the cutoff) and the converted
-// differences; the caller accumulates fac' * (af,bf,cf).  With EV it also
-// accumulates s6 (s6 - 1) (energy / 4 eps) and s6 (2 s6 - 1) (virial / 24 eps).
+// Membership is the exact integer rule 0 < R^2 <= Rc2 with R^2 = a^2 + b^2 +
+// c^2 in 64-bit integers.  The same exact R^2, rounded once to the pair
+// precision, is the r^2 of the force: near the zero of F(r) (r = 2^(1/6)
+// sigma) the force is ill-conditioned in r (|r F'/F| ~ 40), so r^2 carries one
+// rounding instead of the several of a float sum of rounded squares (this
+// cuts the worst FP32 force error relative to RMS|F| about 3x on dilute boxes).
+// Output: fac' (0 outside the cutoff) and the converted differences; the
+// caller accumulates fac' * (af,bf,cf).  With EV it also accumulates
+// s6 (s6 - 1) (energy / 4 eps) and s6 (2 s6 - 1) (virial / 24 eps).
 // ---------------------------------------------------------------------------
-template <bool EV>
+__device__ __forceinline__ uint64_t r2_exact(int a, int b, int c) {
+  return (uint64_t)((long long)a * a) + (uint64_t)((long long)b * b) + (uint64_t)((long long)c * c);
+}
+
+// Coarse r^2 for screening candidates without 64-bit arithmetic: each
+// difference is shifted right by 9 (|a >> 9| < 2^22) and converted exactly by
+// the magic-number method (the bits of 1.5 2^23 + v read as a float are
+// 1.5 2^23 + v), giving A = floor(a / 512).  Since |(a/512)^2 - A^2| <= 2|A| + 1,
+// the exact R^2 / 2^18 lies within 2 (|A|+|B|+|C|) + 3 + rounding of the
+// returned sum; coarse_band() turns that into thresholds below which a pair is
+// certainly inside and above which it is certainly outside.
+__device__ __forceinline__ float coarse_r2(int a, int b, int c) {
+  const float x = __int_as_float((a >> 9) + 0x4B400000) - 12582912.0f;
+  const float y = __int_as_float((b >> 9) + 0x4B400000) - 12582912.0f;
+  const float z = __int_as_float((c >> 9) + 0x4B400000) - 12582912.0f;
+  return fmaf(z, z, fmaf(y, y, x * x));
+}
+
+template <bool EV, bool SCREEN = false>
 __device__ __forceinline__ float pair_f32(int a, int b, int c, const LJParams& P, float& af, float& bf,
                                           float& cf, float& eu, float& ew, int& cnt) {
-  af = __int2float_rn(a);
-  bf = __int2float_rn(b);
-  cf = __int2float_rn(c);
-  const float r2 = fmaf(cf, cf, fmaf(bf, bf, af * af));
-  bool in = (r2 < P.rc2f_lo) & (r2 > 0.0f);
-  if ((r2 >= P.rc2f_lo) & (r2 <= P.rc2f_hi)) in = in_cut_exact(a, b, c, P.Rc2);
+  af = bf = cf = 0.0f;
+  if (SCREEN) {
+    const float r2p = coarse_r2(a, b, c);
+    if (r2p > P.rc2p_hi) return 0.0f;  // certainly outside the cutoff
+  }
+  const uint64_t R2 = r2_exact(a, b, c);
   float fac = 0.0f;
-  if (in) {
+  if (R2 - 1ull < P.Rc2) {  // 0 < R2 <= Rc2 (R2 = 0 wraps to the largest value)
+    af = __int2float_rn(a);
+    bf = __int2float_rn(b);
+    cf = __int2float_rn(c);
+    // R2 to FP32 from its two 32-bit words: 64-bit conversions run on the FP64
+    // pipe (1/80 rate on GB300); the high word is below 2^24 whenever
+    // r_c < L/16, so the sum carries a single rounding
+    const float r2 = fmaf(__uint2float_rn((uint32_t)(R2 >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)R2));
     const float inv = rcp_nr(r2);
     const float s2 = fmaf(inv, P.S_hi, inv * P.S_lo);
     const float s6 = s2 * s2 * s2;
@@ -143,14 +174,14 @@ __device__ __forceinline__ float pair_f32(int a, int b, int c, const LJParams& P
 template <bool EV>
 __device__ __forceinline__ double pair_f64(int a, int b, int c, const LJParams& P, double& ad,
                                            double& bd, double& cd, double& eu, double& ew, int& cnt) {
-  ad = (double)a;
-  bd = (double)b;
-  cd = (double)c;
-  const double r2 = fma(cd, cd, fma(bd, bd, ad * ad));
-  bool in = (r2 < P.rc2d_lo) & (r2 > 0.0);
-  if ((r2 >= P.rc2d_lo) & (r2 <= P.rc2d_hi)) in = in_cut_exact(a, b, c, P.Rc2);
+  const uint64_t R2 = r2_exact(a, b, c);
   double fac = 0.0;
-  if (in) {
+  ad = bd = cd = 0.0;
+  if (R2 - 1ull < P.Rc2) {
+    ad = (double)a;
+    bd = (double)b;
+    cd = (double)c;
+    const double r2 = __ull2double_rn(R2);
     const double inv = 1.0 / r2;
     const double s2 = P.S * inv;
     const double s6 = s2 * s2 * s2;
@@ -170,16 +201,16 @@ template <typename R>
 struct Prec;
 template <>
 struct Prec<float> {
-  template <bool EV>
+  template <bool EV, bool SCREEN = false>
   __device__ __forceinline__ static float pair(int a, int b, int c, const LJParams& P, float& af, float& bf,
                                                float& cf, float& eu, float& ew, int& cnt) {
-    return pair_f32<EV>(a, b, c, P, af, bf, cf, eu, ew, cnt);
+    return pair_f32<EV, SCREEN>(a, b, c, P, af, bf, cf, eu, ew, cnt);
   }
   __device__ __forceinline__ static double to_d(float v) { return f2d_exact(v); }
 };
 template <>
 struct Prec<double> {
-  template <bool EV>
+  template <bool EV, bool SCREEN = false>
   __device__ __forceinline__ static double pair(int a, int b, int c, const LJParams& P, double& ad,
                                                 double& bd, double& cd, double& eu, double& ew, int& cnt) {
     return pair_f64<EV>(a, b, c, P, ad, bd, cd, eu, ew, cnt);
@@ -257,6 +288,7 @@ struct Ctx {
   int nc_lc = 0, nc_vl = 0;
   LJParams P{};            // params with the cutoff r_c
   uint64_t Rl2 = 0;        // floor((r_l/u)^2)
+  float rl2p_lo = 0, rl2p_hi = 0;  // coarse_r2 screening thresholds for r_l
   int64_t n = 0;
   bool have_particles = false;
   bool moved = true;             // particles moved since the last binning
@@ -303,6 +335,9 @@ struct Ctx {
   // Verlet lists
   int32_t* nbr = nullptr;  // row-major [n][cap] (JSPLIT) or column-major [cap][n] (IPT)
   int32_t* nnbr = nullptr;
+  int16_t* nbr16 = nullptr;  // 16-bit copy of nbr (j - i wrapped modulo n) when every entry fits
+  size_t nbr16_cap = 0;
+  bool vl_idx16 = false;
   int vl_cap = 0;
   int vl_half = -1;        // half mode of the current list, -1 = none
   int vl_colmajor = 0;
@@ -330,6 +365,9 @@ struct Ctx {
   double* host_ev = nullptr;  // pinned mirror
   unsigned long long* host_np = nullptr;
   uint32_t* host_status = nullptr;
+
+  // L2 persisting window over the positions for the Verlet-list kernels (0 = off)
+  size_t l2_window_bytes = 0;
 
   // staging buffer for host uploads
   void* stage = nullptr;
@@ -368,6 +406,18 @@ cudaError_t sort_segments(Ctx& c, const uint32_t* starts, int64_t nseg, unsigned
                           unsigned long long* key2);
 cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen);
 cudaError_t launch_reverse_index(Ctx& c);
+cudaError_t launch_list_to16(Ctx& c, uint32_t* overflow);
+
+// Thresholds for coarse_r2 (units of 2^18 u^2) around the integer threshold
+// R2max: certainly inside below *lo, certainly outside above *hi.  The band
+// half-width covers the flooring bound 2 (|A|+|B|+|C|) + 3 <= 2 sqrt(3 x) + 3
+// at x = R2max / 2^18, plus float rounding of the sum, doubled for safety.
+inline void coarse_band(uint64_t R2max, float* lo, float* hi) {
+  const double x = (double)R2max / 262144.0;
+  const double d = 2.0 * (2.0 * std::sqrt(3.0 * x) + 3.0) + 4.0e-7 * x + 8.0;
+  *lo = (float)std::max(0.0, x - d) * (1.0f - 1e-6f);
+  *hi = (float)(x + d) * (1.0f + 1e-6f);
+}
 cudaError_t launch_twopass_gather(Ctx& c);
 cudaError_t force_lc_f32(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t force_lc_f64(Ctx& c, const lj_config& cfg, bool ev);

@@ -91,6 +91,16 @@ _SIGS = {
     "lj_kinetic_energy": (C.c_int, [_VP, C.POINTER(C.c_double)]),
     "lj_timing": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP]),
     "lj_bin_cells_static": (C.c_int, [_VP, C.c_int64, C.c_int32, _VP, _VP, _VP]),
+    "lj_ensemble_create": (C.c_int, [C.POINTER(_VP), C.c_int32, _VP, _VP, _VP, _VP, C.c_double, C.c_double,
+                                     C.c_double, C.c_double, _VP]),
+    "lj_ensemble_run": (C.c_int, [_VP, C.c_double, C.c_int32, C.c_int32]),
+    "lj_ensemble_tune": (C.c_int, [_VP, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lj_ensemble_get": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "lj_ensemble_debug": (C.c_int, [_VP, C.c_uint32, C.c_int32]),
+    "lj_ensemble_size": (C.c_int64, [_VP]),
+    "lj_ensemble_uses_graph": (C.c_int32, [_VP]),
+    "lj_ensemble_last_error": (C.c_char_p, [_VP]),
+    "lj_ensemble_destroy": (None, [_VP]),
     "lj_last_error": (C.c_char_p, [_VP]),
     "lj_destroy": (None, [_VP]),
 }
@@ -294,6 +304,72 @@ class Domain:
         arr = (lj_config * C_out)(*cfgs)
         self._check(self.lib.lj_tuner_set_model(self.h, p.ctypes.data, C_out, m.ctypes.data, s.ctypes.data,
                                                 C.cast(arr, _VP)))
+
+
+class Ensemble:
+    """Many independent boxes advanced by one persistent launch (lj_ensemble_*)."""
+
+    def __init__(self, systems, rc=2.5, eps=1.0, sigma=1.0, mass=1.0, stream=None):
+        self.lib = load()
+        self.h = _VP()
+        self.systems = systems
+        Ls = np.array([s.L for s in systems], dtype=np.float64)
+        counts = np.array([s.n for s in systems], dtype=np.int64)
+        pos = np.concatenate([np.ascontiguousarray(s.pos, dtype=np.uint32).ravel() for s in systems])
+        vel = np.concatenate([np.ascontiguousarray(s.vel, dtype=np.float64).ravel() for s in systems])
+        st = self.lib.lj_ensemble_create(C.byref(self.h), len(systems), Ls.ctypes.data, counts.ctypes.data,
+                                         pos.ctypes.data, vel.ctypes.data, rc, eps, sigma, mass,
+                                         _stream_ptr(stream))
+        if st != LJ_OK:
+            raise LJError(st, "lj_ensemble_create failed")
+        self.counts = counts
+        self.n = int(counts.sum())
+
+    def run(self, dt, nsteps, use_graph=True):
+        st = self.lib.lj_ensemble_run(self.h, dt, nsteps, int(bool(use_graph)))
+        if st != LJ_OK:
+            raise LJError(st, "lj_ensemble_run failed")
+
+    def tune(self, dt=0.002, steps=10):
+        w, b = C.c_int32(), C.c_int32()
+        st = self.lib.lj_ensemble_tune(self.h, dt, steps, C.byref(w), C.byref(b))
+        if st != LJ_OK:
+            raise LJError(st, "lj_ensemble_tune failed")
+        return w.value, b.value
+
+    def state(self):
+        pos = np.zeros(3 * self.n, dtype=np.uint32)
+        vel = np.zeros(3 * self.n)
+        frc = np.zeros(3 * self.n)
+        st = self.lib.lj_ensemble_get(self.h, pos.ctypes.data, vel.ctypes.data, frc.ctypes.data)
+        if st != LJ_OK:
+            raise LJError(st, "lj_ensemble_get failed")
+        out, off = [], 0
+        for nb in self.counts:
+            sl = slice(3 * off, 3 * (off + nb))
+            out.append((pos[sl].reshape(3, nb), vel[sl].reshape(3, nb), frc[sl].reshape(3, nb)))
+            off += nb
+        return out
+
+    def uses_graph(self):
+        return bool(self.lib.lj_ensemble_uses_graph(self.h))
+
+    def last_error(self):
+        return self.lib.lj_ensemble_last_error(self.h).decode()
+
+    def debug(self, spin_limit=0, skip_block=-1):
+        self.lib.lj_ensemble_debug(self.h, spin_limit, skip_block)
+
+    def close(self):
+        if self.h:
+            self.lib.lj_ensemble_destroy(self.h)
+            self.h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tune_select(timings, valid=None, reduce=0) -> int:
