@@ -7,7 +7,9 @@ homogeneous LJ fluid, 1,048,576 particles at density 0.75 in a periodic cube
 (L = 111.82), cutoff 2.5, Verlet skin 0.3 rebuilt every 10 steps,
 Maxwell-Boltzmann velocities at T = 1.0, dt = 0.002; FP32 pair arithmetic with
 FP64 accumulation.  The configuration (container x interaction order x
-Newton-3) is picked by the library's full-search tuner before timing.
+Newton-3) is picked by the library's learned tuner (committed network trained on
+GB300 full-search timings); full search also runs and gives the best fixed
+order, reported beside the learned choice.
 
 Metric: unique in-cutoff pair evaluations per second (a pair counts once per
 force evaluation whatever the Newton-3 setting), whole job over all ranks.
@@ -53,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1048576)
-    ap.add_argument("--tune", default="full", choices=["full", "fixed"])
+    ap.add_argument("--tune", default="learned", choices=["learned", "full", "fixed"])
     ap.add_argument("--cfg", default=None, help="fixed configuration, e.g. 1,5,0,1 (container,order,param,n3)")
     ap.add_argument("--samples", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
@@ -200,14 +202,28 @@ def run_ours(args, ws, rank, local, pg):
     d.set_particles(pos_d, vel_d)
 
     # configuration: full search (Sec. 2.3.2) over every valid configuration
-    times = {}
-    if args.tune == "full":
+    # gives the best fixed order; the learned tuner (committed network trained
+    # on GB300 timings of the density sweep) picks from the features alone
+    times, learned_info = {}, None
+    if args.tune in ("full", "learned"):
         cfg, times = d.tune(0, args.samples)
+        if args.tune == "learned":
+            from paper_2512_03565_gb300 import tuner
+            tuner.install(d, tuner.load())
+            t0 = time.perf_counter()
+            lcfg, _ = d.tune(1, 0)
+            t_learn = time.perf_counter() - t0
+            lname = lj.config_name(lcfg)
+            learned_info = {"choice": lname, "tuning_ms": 1e3 * t_learn,
+                            "full_search_choice": lj.config_name(cfg)}
+            cfg = lcfg
     else:
         cfg = lj.config(*[int(v) for v in (args.cfg or "1,5,0,1").split(",")])
     cfg_name = lj.config_name(cfg)
     timed = {k: v for k, v in times.items() if not math.isnan(v)}
     best_fixed = min(timed.items(), key=lambda kv: kv[1]) if timed else (cfg_name, None)
+    if learned_info is not None:
+        learned_info["time_over_best_fixed"] = timed[cfg_name] / best_fixed[1]
 
     dt, rebuild = 0.002, 10
     for _ in range(args.warmup):
@@ -294,7 +310,7 @@ def run_ours(args, ws, rank, local, pg):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": s.n, "config": cfg_name, "tuner": args.tune,
                    "cfg_tuple": [cfg.container, cfg.order, cfg.param, cfg.newton3],
-                   "best_fixed": best_fixed[0], "best_fixed_ms": best_fixed[1],
+                   "best_fixed": best_fixed[0], "best_fixed_ms": best_fixed[1], "learned": learned_info,
                    "tuned_force_ms": times.get(cfg_name), "pairs_per_step": float(np.mean(pairs)),
                    "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{ws}",
                    "wall_s": t_wall, "tuning_times_ms": timed},

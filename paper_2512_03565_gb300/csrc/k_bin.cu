@@ -290,10 +290,13 @@ cudaError_t bin_cells(Ctx& c, int nc) {
 // tile = (begin, end, row, cx_first | cx_last << 16).
 // -------------------------------------------------------------------------
 template <bool WRITE>
-__global__ void k_row_tiles(const uint32_t* __restrict__ cs, int nc, int T, uint32_t* __restrict__ row_cnt,
+__global__ void k_row_tiles(const uint32_t* __restrict__ cs, int nc, int Tsigned, uint32_t* __restrict__ row_cnt,
                             uint4* __restrict__ tiles) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nc * nc) return;
+  // T < 0: tiles of at most |T| particles of a single cell
+  const int T = Tsigned < 0 ? -Tsigned : Tsigned;
+  const int maxspan = Tsigned < 0 ? 0 : nc - 3;
   uint32_t k = WRITE ? row_cnt[r] : 0u;
   uint32_t tb = 0, tn = 0;
   int cf = 0, cl = 0;
@@ -301,7 +304,7 @@ __global__ void k_row_tiles(const uint32_t* __restrict__ cs, int nc, int T, uint
   for (int cx = 0; cx < nc; ++cx) {
     uint32_t a = cs[(int64_t)r * nc + cx], b = cs[(int64_t)r * nc + cx + 1];
     while (a < b) {
-      if (open && (tn == (uint32_t)T || cx - cf > nc - 3)) {
+      if (open && (tn == (uint32_t)T || cx - cf > maxspan)) {
         if (WRITE) tiles[k] = make_uint4(tb, tb + tn, (uint32_t)r, (uint32_t)cf | ((uint32_t)cl << 16));
         ++k;
         open = false;

@@ -74,14 +74,21 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
     if (vi) {
       const uint4 pi = A.pos[i];
       const int m = min(A.nnbr[i], A.cap);
+      // software pipeline: the next batch's list entries load while the
+      // current batch's positions are gathered and its pairs computed
+      int jc[VL_BATCH];
+#pragma unroll
+      for (int t = 0; t < VL_BATCH; ++t) jc[t] = (t < m) ? vl_entry<I16>(A, (int64_t)t * n + i, i, n) : (int)i;
       for (int k0 = 0; k0 < m; k0 += VL_BATCH) {
-        int jj[VL_BATCH];
         uint4 pj[VL_BATCH];
 #pragma unroll
-        for (int t = 0; t < VL_BATCH; ++t)
-          jj[t] = (k0 + t < m) ? vl_entry<I16>(A, (int64_t)(k0 + t) * n + i, i, n) : (int)i;
+        for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jc[t]);
+        int jn[VL_BATCH];
 #pragma unroll
-        for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jj[t]);
+        for (int t = 0; t < VL_BATCH; ++t) {
+          const int k = k0 + VL_BATCH + t;
+          jn[t] = (k < m) ? vl_entry<I16>(A, (int64_t)k * n + i, i, n) : (int)i;
+        }
 #pragma unroll
         for (int t = 0; t < VL_BATCH; ++t) {
           R af, bf, cf;
@@ -91,9 +98,9 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
           fy += fac * bf;
           fz += fac * cf;
           if (N3 == 1) {
-            vl_atomic(out.fx + jj[t], fac * af, P.e24u);
-            vl_atomic(out.fy + jj[t], fac * bf, P.e24u);
-            vl_atomic(out.fz + jj[t], fac * cf, P.e24u);
+            vl_atomic(out.fx + jc[t], fac * af, P.e24u);
+            vl_atomic(out.fy + jc[t], fac * bf, P.e24u);
+            vl_atomic(out.fz + jc[t], fac * cf, P.e24u);
           } else if (N3 == 2) {
             if (k0 + t < m) {
               const int64_t e = (int64_t)(k0 + t) * n + i;
@@ -105,6 +112,8 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
             }
           }
         }
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t) jc[t] = jn[t];
       }
       if (N3 == 1) {
         vl_atomic(out.fx + i, fx, -P.e24u);
@@ -139,14 +148,19 @@ __global__ void __launch_bounds__(256) k_vl_jsplit(LJParams P, VLArgs A, ForceOu
       const uint4 pi = A.pos[i];
       const int m = min(A.nnbr[i], A.cap);
       const int64_t row = i * A.cap;
+      int jc[VL_BATCH];
+#pragma unroll
+      for (int t = 0; t < VL_BATCH; ++t) jc[t] = (sub + t * W < m) ? vl_entry<I16>(A, row + sub + t * W, i, n) : (int)i;
       for (int k0 = sub; k0 < m; k0 += W * VL_BATCH) {
-        int jj[VL_BATCH];
         uint4 pj[VL_BATCH];
 #pragma unroll
-        for (int t = 0; t < VL_BATCH; ++t)
-          jj[t] = (k0 + t * W < m) ? vl_entry<I16>(A, row + k0 + t * W, i, n) : (int)i;
+        for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jc[t]);
+        int jn[VL_BATCH];
 #pragma unroll
-        for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jj[t]);
+        for (int t = 0; t < VL_BATCH; ++t) {
+          const int k = k0 + W * VL_BATCH + t * W;
+          jn[t] = (k < m) ? vl_entry<I16>(A, row + k, i, n) : (int)i;
+        }
 #pragma unroll
         for (int t = 0; t < VL_BATCH; ++t) {
           R af, bf, cf;
@@ -156,11 +170,13 @@ __global__ void __launch_bounds__(256) k_vl_jsplit(LJParams P, VLArgs A, ForceOu
           fy += fac * bf;
           fz += fac * cf;
           if (N3 == 1) {
-            vl_atomic(out.fx + jj[t], fac * af, P.e24u);
-            vl_atomic(out.fy + jj[t], fac * bf, P.e24u);
-            vl_atomic(out.fz + jj[t], fac * cf, P.e24u);
+            vl_atomic(out.fx + jc[t], fac * af, P.e24u);
+            vl_atomic(out.fy + jc[t], fac * bf, P.e24u);
+            vl_atomic(out.fz + jc[t], fac * cf, P.e24u);
           }
         }
+#pragma unroll
+        for (int t = 0; t < VL_BATCH; ++t) jc[t] = jn[t];
       }
     }
 #pragma unroll

@@ -2,8 +2,9 @@
 // particles within cutoff + skin, built with the help of the linked-cell
 // structure and rebuilt every few steps).
 //
-// The builder walks row tiles (<= 32 consecutive particles of one cell row,
-// the tiles of the linked-cell kernels): a warp loads each 32-particle chunk of
+// The builder walks tiles of <= 32 consecutive particles of one cell (so a
+// tile's candidates are exactly the 27 cells around it): a warp loads each
+// 32-particle chunk of
 // the tile's neighbour segments once, then for every i of the tile tests the
 // chunk's 32 j's (one per lane) with the exact integer rule, keeps j != i with
 // 0 < R^2 <= floor((r_l/u)^2) (half lists: j > i), and compacts the survivors
@@ -138,7 +139,7 @@ static inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t)
 
 cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen) {
   const int64_t n = c.n;
-  cudaError_t e = build_tiles(c, 32);
+  cudaError_t e = build_tiles(c, -32);  // single-cell tiles: exact 27-cell candidate sets
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c.tile_ctr, 0, sizeof(uint32_t), c.stream)) != cudaSuccess) return e;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8);

@@ -11,7 +11,8 @@
 //
 // Learned: the MLP (k_mlp.cu) predicts the log time of its configurations
 // from the 16 features; the best predicted valid configuration is taken, or
-// the fastest of the top `samples` predictions after timing them.
+// the fastest of the top `samples` predictions after timing them.  Systems
+// whose standardised features lie beyond kMaxFeatureZ fall back to full search.
 #include <cmath>
 #include <limits>
 #include <numeric>
@@ -25,6 +26,10 @@ cudaError_t mlp_forward_dev(const float* d_params, int C, const float* d_X, int6
 using namespace ljgb;
 
 namespace {
+
+// A standardised feature beyond this many training standard deviations puts
+// the system outside the learned tuner's training data.
+constexpr double kMaxFeatureZ = 8.0;
 
 lj_status tfail(Ctx& c, lj_status s, const std::string& m) {
   c.err = m;
@@ -139,7 +144,15 @@ lj_status lj_tune(lj_ctx* h, int32_t kind, int32_t samples, lj_config* chosen, d
     lj_status st = lj_features(h, f);
     if (st != LJ_OK) return st;
     float xin[16];
-    for (int k = 0; k < 16; ++k) xin[k] = (float)((f[k] - c.mlp_mean[k]) / (c.mlp_std[k] > 0 ? c.mlp_std[k] : 1.0f));
+    bool in_range = true;
+    for (int k = 0; k < 16; ++k) {
+      xin[k] = (float)((f[k] - c.mlp_mean[k]) / (c.mlp_std[k] > 0 ? c.mlp_std[k] : 1.0f));
+      if (!(std::fabs(xin[k]) <= kMaxFeatureZ)) in_range = false;
+    }
+    if (!in_range) {
+      // the system lies outside the training data: full search instead
+      return lj_tune(h, 0, samples > 0 ? samples : 1, chosen, times_ms);
+    }
     float *dp = nullptr, *dx = nullptr, *dy = nullptr;
     std::vector<float> y(c.mlp_C);
     cudaError_t e = cudaMalloc(&dp, c.mlp_params.size() * sizeof(float));

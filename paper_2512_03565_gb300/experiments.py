@@ -1,0 +1,182 @@
+"""Experiment drivers for the tuned force path (run on a GB300).
+
+* ``density_sweep``: labelled rows for the learned tuner: the 24 density-sweep
+  boxes (16 homogeneous, rho 0.05..1.2; 8 liquid/vapour slabs) at cutoffs 2.5
+  and 3.0, each timed by full search (every configuration) on snapshots of a
+  short MD run.
+* ``leave_one_out``: trains the network without the rows of one box and ranks
+  that box's configurations; reports the regret of the learned choice against
+  the measured best and against a fixed default order.
+* ``droplet``: the expanding droplet (FCC liquid sphere in a vacuum box)
+  integrated for many steps with re-tuning every ``phase`` steps, in three arms:
+  full search at every phase, the learned tuner, and the best single fixed
+  configuration in hindsight (from the full-search evidence of every phase).
+
+Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet [options]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import ljgb as lj
+from . import tuner
+from . import workloads as W
+
+
+def density_sweep(scale=1.0, cutoffs=(2.5, 3.0), snapshots=(0, 50, 100), samples=3, out=None, log=print,
+                  vacuum=True):
+    X, T, labels, box_ids = [], [], [], []
+    names = None
+    box = 0
+    for rc in cutoffs:
+        systems = W.config3(rc=rc, scale=scale) + (W.vacuum_extension(rc) if vacuum else [])
+        for s in systems:
+            t0 = time.time()
+            x, t, nm, lb = tuner.collect([s], samples=samples, snapshots=snapshots)
+            names = nm
+            X.append(x)
+            T.append(t)
+            labels += lb
+            box_ids += [box] * x.shape[0]
+            box += 1
+            log(f"{s.name} rc={rc}: {x.shape[0]} rows in {time.time() - t0:.1f} s")
+    X, T = np.concatenate(X), np.concatenate(T)
+    if out:
+        np.savez(out, X=X, T=T, names=np.array(names), labels=np.array(labels), box=np.array(box_ids))
+    return X, T, names, labels, np.array(box_ids)
+
+
+def regret_of(pred, t_row, mask_row):
+    """Time of the predicted best valid configuration over the measured best."""
+    p = np.where(mask_row, pred, np.inf)
+    k = int(np.argmin(p))
+    best = np.nanmin(np.where(mask_row, t_row, np.nan))
+    return t_row[k] / best, k
+
+
+def leave_one_out(X, T, box_ids, names, epochs=2000, lr=3e-3, default="VL:JSPLIT-32:N3off", log=print):
+    _, M = tuner.targets(T)
+    M = M.astype(bool)
+    res = []
+    d_idx = names.index(default) if default in names else None
+    for b in np.unique(box_ids):
+        tr, te = box_ids != b, box_ids == b
+        model = tuner.train(X[tr], T[tr], epochs=epochs, lr=lr)
+        pred = tuner.predict(model, X[te])
+        for r, row in enumerate(np.where(te)[0]):
+            reg, k = regret_of(pred[r], T[row], M[row])
+            best = np.nanmin(np.where(M[row], T[row], np.nan))
+            dflt = T[row, d_idx] / best if d_idx is not None and M[row, d_idx] else float("nan")
+            res.append({"box": int(b), "row": int(row), "learned_regret": float(reg),
+                        "learned_choice": names[k], "best": names[int(np.nanargmin(np.where(M[row], T[row], np.nan)))],
+                        "default_regret": float(dflt)})
+        log(f"box {b}: mean regret {np.mean([x['learned_regret'] for x in res if x['box'] == b]):.3f}")
+    return res
+
+
+def droplet(radius=84.19, steps=10000, phase=500, samples=3, arms=("exhaustive", "learned"), model_path=None,
+            confirm=2, dt=0.002, log=print):
+    """Expanding droplet with re-tuning every `phase` steps.  Per phase each arm
+    records the tuning time and the synchronised wall time of integrating the
+    phase (force kernels, list builds, binning, integration).  The hindsight
+    best fixed configuration comes from the full-search evidence."""
+    s = W.config4(radius)
+    log(f"droplet: n={s.n} L={s.L:.1f}")
+    out = {"n": s.n, "L": s.L, "steps": steps, "phase": phase, "arms": {}}
+    names = [lj.config_name(c) for c in lj.configs()]
+    evidence = []
+    for arm in arms:
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos, s.vel)
+        if arm == "learned":
+            tuner.install(d, tuner.load(model_path or tuner.MODEL_PATH))
+        run_ms, force_ms, tune_ms, tune_evals, choices, phase_ms = 0.0, 0.0, 0.0, 0, [], []
+        for ph in range(steps // phase):
+            d.counters()
+            t0 = time.perf_counter()
+            if arm == "exhaustive":
+                cfg, times = d.tune(0, samples)
+                evidence.append([times.get(nm, float("nan")) for nm in names])
+                tune_evals += sum(1 for v in times.values() if not math.isnan(v)) * (samples + 1)
+            else:
+                cfg, times = d.tune(1, confirm)
+                n_timed = sum(1 for v in times.values() if not math.isnan(v))
+                tune_evals += n_timed * (3 + 1)
+            tune_ms += (time.perf_counter() - t0) * 1e3
+            d.timing(1)
+            d.counters()
+            t0 = time.perf_counter()
+            d.integrate(dt, phase, cfg)
+            d.counters()  # synchronises
+            pm = (time.perf_counter() - t0) * 1e3
+            fms, _, _ = d.timing(0)
+            run_ms += pm
+            force_ms += fms
+            phase_ms.append(pm)
+            choices.append(lj.config_name(cfg))
+            log(f"{arm} phase {ph}: {lj.config_name(cfg)} run {pm:.1f} ms force {fms:.1f} ms")
+        out["arms"][arm] = {"run_ms": run_ms, "force_ms": force_ms, "tune_ms": tune_ms, "tune_evals": tune_evals,
+                            "tuning_step_fraction": tune_evals / steps, "choices": choices, "phase_ms": phase_ms}
+        d.close()
+    if evidence:
+        E = np.array(evidence)
+        tot = np.nansum(np.where(np.isfinite(E), E, np.inf), axis=0)
+        k = int(np.argmin(tot))
+        out["best_fixed_in_hindsight"] = names[k]
+        out["evidence"] = {"names": names, "ms": E.tolist()}
+    if "exhaustive" in out["arms"] and "learned" in out["arms"]:
+        ex, le = out["arms"]["exhaustive"], out["arms"]["learned"]
+        out["learned_over_exhaustive_run"] = le["run_ms"] / ex["run_ms"]
+        out["learned_over_exhaustive_with_tuning"] = (le["run_ms"] + le["tune_ms"]) / (ex["run_ms"] + ex["tune_ms"])
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["sweep", "train", "droplet"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--data", default="gpurun_out/tuner_data.npz")
+    ap.add_argument("--model", default=tuner.MODEL_PATH)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--phase", type=int, default=500)
+    ap.add_argument("--radius", type=float, default=84.19)
+    ap.add_argument("--loo", action="store_true")
+    a = ap.parse_args(argv)
+    from . import build as B
+    B.build()
+    if a.what == "sweep":
+        density_sweep(scale=a.scale, out=a.data)
+    elif a.what == "train":
+        z = np.load(a.data)
+        X, T, names, box = z["X"], z["T"], [str(v) for v in z["names"]], z["box"]
+        model = tuner.train(X, T, epochs=a.epochs)
+        tuner.save(model, names, a.model, meta={"rows": int(X.shape[0]), "epochs": a.epochs,
+                                                "final_loss": float(model["losses"][-1])})
+        print(f"trained: rows={X.shape[0]} loss {model['losses'][0]:.4f} -> {model['losses'][-1]:.4f}")
+        if a.loo:
+            res = leave_one_out(X, T, box, names, epochs=a.epochs)
+            summ = {"mean_learned_regret": float(np.mean([r["learned_regret"] for r in res])),
+                    "max_learned_regret": float(np.max([r["learned_regret"] for r in res])),
+                    "mean_default_regret": float(np.nanmean([r["default_regret"] for r in res])),
+                    "rows": res}
+            print(json.dumps({k: v for k, v in summ.items() if k != "rows"}))
+            if a.out:
+                json.dump(summ, open(a.out, "w"))
+    else:
+        res = droplet(a.radius, a.steps, a.phase, model_path=a.model)
+        print(json.dumps({k: v for k, v in res.items() if k != "evidence"}))
+        if a.out:
+            json.dump(res, open(a.out, "w"))
+
+
+if __name__ == "__main__":
+    main()

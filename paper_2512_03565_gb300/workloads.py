@@ -208,6 +208,39 @@ def ensemble(nboxes: int = 256, nmin: int = 500, nmax: int = 50000, rho_lo: floa
     return [homogeneous(int(n), float(r), int(s), T, **kw) for n, r, s in zip(ns, rhos, seeds)]
 
 
+def exploding_cube(n: int, rho: float = 0.9, box_factor: float = 3.0, seed: int = BASE_SEED + 5,
+                   T: float = 1.2, **kw) -> System:
+    """Dense jittered-FCC cube of n particles at density rho centred in a periodic
+    vacuum box of edge box_factor x the cube's edge (the shape of the paper's
+    "Exploding Cube" benchmark, Sec. 5.1)."""
+    rng = np.random.default_rng(seed)
+    side = (n / rho) ** (1.0 / 3.0)
+    L = box_factor * side
+    m = 1
+    while 4 * m ** 3 < n:
+        m += 1
+    pts = fcc_sites(m)
+    if pts.shape[1] > n:
+        pts = pts[:, np.sort(rng.choice(pts.shape[1], size=n, replace=False))]
+    pts = pts + rng.uniform(-0.02, 0.02, size=pts.shape) / m
+    frac = 0.5 + (pts - 0.5) * (side / L)
+    return System(L=L, pos=_frac_to_fp(frac), vel=maxwell_boltzmann(rng, n, T),
+                  name=f"cube n={n} factor={box_factor}", **kw)
+
+
+def vacuum_extension(rc: float = 2.5, seed: int = BASE_SEED + 6) -> list:
+    """Inhomogeneous, vacuum-dominated systems that extend the density sweep:
+    liquid spheres (R 20, 30, 45) in boxes of 4x their diameter and dense cubes in
+    boxes of 3x and 5x their edge -- all smaller than the expanding-droplet
+    workload, which stays out of the training data."""
+    out = []
+    for k, R in enumerate([20.0, 30.0, 45.0]):
+        out.append(droplet(R, 0.8, seed + k, T=1.2, rc=rc, skin=0.3))
+    for k, (n, f) in enumerate([(100000, 3.0), (300000, 5.0)]):
+        out.append(exploding_cube(n, 0.9, f, seed + 10 + k, T=1.2, rc=rc, skin=0.3))
+    return out
+
+
 # --- the named workloads ---------------------------------------------------
 
 def config1() -> System:

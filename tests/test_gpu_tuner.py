@@ -1,0 +1,72 @@
+"""Run-time tuning on the GPU: full search (Sec. 2.3.2) and the learned tuner
+(Sec. 6's data-driven tuning) with the committed model trained on GB300
+timings of the density sweep."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2512_03565_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lj():
+    from paper_2512_03565_gb300 import build as b
+    b.build()
+    from paper_2512_03565_gb300 import ljgb
+    ljgb.load()
+    return ljgb
+
+
+def test_full_search_returns_argmin_of_its_evidence(lj):
+    s = W.stratified(60000, 0.6, 41)
+    d = lj.Domain(s.L, s.rc, s.skin)
+    d.set_particles(s.pos, s.vel)
+    cfg, times = d.tune(0, 2)
+    timed = {k: v for k, v in times.items() if not np.isnan(v)}
+    assert len(timed) == 33
+    assert lj.config_name(cfg) == min(timed, key=timed.get)
+    d.close()
+
+
+def test_learned_tuner_without_model_falls_back_to_full_search(lj):
+    s = W.stratified(20000, 0.5, 42)
+    d = lj.Domain(s.L, s.rc, s.skin)
+    d.set_particles(s.pos, s.vel)
+    cfg, times = d.tune(1, 1)
+    assert lj.load().lj_config_valid(cfg)
+    assert sum(not np.isnan(v) for v in times.values()) == 33
+    d.close()
+
+
+@pytest.mark.parametrize("system", [
+    lambda: W.stratified(300000, 0.4, 999),
+    lambda: W.slab(400000, 0.8, 0.02, 0.5, 998),
+    lambda: W.fcc(250000, 1.0, 997),
+], ids=["fluid-0.4", "slab-0.5", "fcc-1.0"])
+def test_learned_tuner_gain_on_held_out_systems(lj, system):
+    """The learned choice (features -> network, no timing) is measured against
+    full search on systems absent from the training data; it must be within
+    15% of the measured best, no worse than the paper's default order (1/V, here
+    VL:JSPLIT-32), and cost a small fraction of full search's tuning time."""
+    from paper_2512_03565_gb300 import tuner
+    s = system()
+    model = tuner.load()
+    d = lj.Domain(s.L, s.rc, s.skin)
+    d.set_particles(s.pos, s.vel)
+    t0 = time.perf_counter()
+    _, times = d.tune(0, 3)
+    t_full = time.perf_counter() - t0
+    tuner.install(d, model)
+    t0 = time.perf_counter()
+    learned, _ = d.tune(1, 0)
+    t_learned = time.perf_counter() - t0
+    d.close()
+    best = min(v for v in times.values() if not np.isnan(v))
+    t_l = times[lj.config_name(learned)]
+    t_default = times["VL:JSPLIT-32:N3off"]
+    assert t_l <= 1.15 * best, (lj.config_name(learned), t_l, best)
+    assert t_l <= t_default * 1.02
+    assert t_learned < 0.1 * t_full

@@ -1,0 +1,40 @@
+"""CPU checks of the committed learned-tuner model and its training data.
+
+The network is evaluated with the FP64 oracle's forward pass (independent of
+the GPU kernels that trained it): it must rank the configurations of its own
+training rows (GB300 full-search timings of the density sweep) close to the
+measured best."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_03565_gb300 import tuner
+
+
+def test_targets_are_relative_log_times():
+    T = np.array([[2.0, 1.0, np.nan, 4.0], [3.0, 3.0, 6.0, 1.5]])
+    Y, M = tuner.targets(T)
+    np.testing.assert_allclose(Y[0], [np.log(2.0), 0.0, 0.0, np.log(4.0)])
+    np.testing.assert_allclose(Y[1], [np.log(2.0), np.log(2.0), np.log(4.0), 0.0])
+    np.testing.assert_array_equal(M, [[1, 1, 0, 1], [1, 1, 1, 1]])
+
+
+def test_committed_model_ranks_its_training_rows():
+    import os
+    path = os.path.join(os.path.dirname(tuner.MODEL_PATH), "tuner_data.npz")
+    z = np.load(path)
+    X, T = z["X"], z["T"]
+    z2 = np.load(tuner.MODEL_PATH)
+    params, mean, std, C = z2["params"].astype(np.float64), z2["mean"], z2["std"], int(z2["C"])
+    assert params.shape[0] == oracle.mlp_nparams(C) and C == T.shape[1]
+    oracle.build()
+    Y = oracle.mlp_forward(params, C, (X - mean) / std)
+    _, M = tuner.targets(T)
+    regrets = []
+    for r in range(X.shape[0]):
+        p = np.where(M[r] > 0, Y[r], np.inf)
+        k = int(np.argmin(p))
+        regrets.append(T[r, k] / np.nanmin(np.where(M[r] > 0, T[r], np.nan)))
+    regrets = np.array(regrets)
+    assert np.median(regrets) <= 1.02
+    assert np.mean(regrets) <= 1.05
