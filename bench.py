@@ -270,10 +270,20 @@ def run_ours(args, ws, rank, local, pg):
     flops_launch = FLOPS_PER_PAIR[cfg.newton3] * float(np.mean(pairs))
     achieved = flops_launch / avg_force_s / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = traffic_from_profiles(cfg_name)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_from_profiles(cfg_name), "kernel_ms": avg_force_s * 1e3,
+            "traffic": traffic, "kernel_ms": avg_force_s * 1e3,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FFMA)",
             "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3]}
+    if traffic:
+        hbm_peak = 6800.0
+        try:
+            hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        except Exception:
+            pass
+        roof["hbm_gbs"] = traffic / avg_force_s / 1e9
+        roof["hbm_frac"] = roof["hbm_gbs"] / hbm_peak
+        roof["hbm_peak_gbs"] = hbm_peak
 
     # end to end through the public API with host buffers: positions (doubles)
     # from pinned host memory in, one force evaluation, forces back to host

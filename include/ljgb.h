@@ -280,6 +280,9 @@ lj_status lj_ensemble_get(lj_ens* ens, uint32_t* pos_fp, double* vel, double* fr
  * a block that leaves before its first barrier (-1 = none). */
 lj_status lj_ensemble_debug(lj_ens* ens, uint32_t spin_limit, int32_t skip_block);
 int64_t lj_ensemble_size(const lj_ens* ens);
+/* Unique in-cutoff pairs summed over the force evaluations since the last
+ * call (resets the count; synchronises); -1 on error. */
+int64_t lj_ensemble_pairs(lj_ens* ens);
 /* Message of the last ensemble error or fallback (never NULL). */
 const char* lj_ensemble_last_error(const lj_ens* ens);
 /* 1 if the last run replayed a captured CUDA graph. */

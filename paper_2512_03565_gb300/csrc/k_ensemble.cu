@@ -58,6 +58,7 @@ struct EnsArgs {
   uint32_t* scan_tot;    // per scan tile
   unsigned* bar;         // [0] arrivals, [1] generation
   uint32_t* status;
+  unsigned long long* npairs;  // in-cutoff pair evaluations (each pair counted from both sides)
   double hdtm;
   int nsteps;
   int first_force;       // compute forces at the initial positions first
@@ -212,6 +213,10 @@ __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __rest
       ay += __shfl_xor_sync(0xffffffffu, ay, o);
       az += __shfl_xor_sync(0xffffffffu, az, o);
     }
+    unsigned long long wc = (unsigned long long)cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
+    if (lane == 0 && wc) atomicAdd(A.npairs, wc);
     if (vi && sub == 0) {
       const double f0 = -B.e24u * f2d_exact(ax), f1 = -B.e24u * f2d_exact(ay), f2 = -B.e24u * f2d_exact(az);
       fx[i] = f0;
@@ -529,6 +534,7 @@ lj_status lj_ensemble_create(lj_ens** out, int32_t nboxes, const double* box_L, 
   M(A.scan_tot, sizeof(uint32_t) * (E.ncells / 256 + 64));
   M(A.bar, sizeof(unsigned) * 2);
   M(A.status, sizeof(uint32_t));
+  M(A.npairs, sizeof(unsigned long long));
   if (e != cudaSuccess) {
     lj_ensemble_destroy(h);
     return LJ_ERR_OOM;
@@ -555,6 +561,7 @@ lj_status lj_ensemble_create(lj_ens** out, int32_t nboxes, const double* box_L, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(A.vel, hv.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(A.frc, 0, sizeof(double) * 3 * n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(A.status, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.npairs, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     lj_ensemble_destroy(h);
@@ -781,6 +788,17 @@ int64_t lj_ensemble_size(const lj_ens* h) { return h ? h->e.ntot : 0; }
 
 const char* lj_ensemble_last_error(const lj_ens* h) { return h ? h->e.err.c_str() : "null ensemble"; }
 
+// Unique in-cutoff pairs summed over all force evaluations since the last
+// call (each pair is evaluated from both sides); resets the count.  Synchronises.
+int64_t lj_ensemble_pairs(lj_ens* h) {
+  if (!h) return -1;
+  unsigned long long v = 0;
+  if (cudaMemcpyAsync(&v, h->e.A.npairs, sizeof(v), cudaMemcpyDeviceToHost, h->e.stream) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(h->e.A.npairs, 0, sizeof(v), h->e.stream) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(h->e.stream) != cudaSuccess) return -1;
+  return (int64_t)(v / 2);
+}
+
 int32_t lj_ensemble_uses_graph(const lj_ens* h) { return h && h->e.last_run_graph ? 1 : 0; }
 
 void lj_ensemble_destroy(lj_ens* h) {
@@ -791,7 +809,7 @@ void lj_ensemble_destroy(lj_ens* h) {
   if (E.graph) cudaGraphDestroy(E.graph);
   EnsArgs& A = E.A;
   void* ps[] = {(void*)A.boxes, (void*)A.box_of, A.pos, A.pos_alt, A.vel, A.vel_alt, A.frc, A.frc_alt, A.cnt,
-                A.cell_start, A.cell_of, A.slot, A.key, A.key2, A.scan_tot, A.bar, A.status};
+                A.cell_start, A.cell_of, A.slot, A.key, A.key2, A.scan_tot, A.bar, A.status, A.npairs};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (E.own_stream) cudaStreamDestroy(E.stream);

@@ -12,7 +12,10 @@
   full search at every phase, the learned tuner, and the best single fixed
   configuration in hindsight (from the full-search evidence of every phase).
 
-Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet [options]
+* ``ensemble``: the 256-box batch in one persistent launch vs the same boxes
+  run one after another.
+
+Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble [options]
 """
 from __future__ import annotations
 
@@ -138,9 +141,55 @@ def droplet(radius=84.19, steps=10000, phase=500, samples=3, arms=("exhaustive",
     return out
 
 
+def ensemble(nboxes=256, steps=1000, dt=0.002, seq_boxes=None, log=print):
+    """The batched ensemble: `nboxes` boxes (N log-uniform in [500, 50000], rho
+    uniform in [0.1, 1.0]) for `steps` steps in one persistent launch per run,
+    replayed as a CUDA graph, after the launch-shape autotuner; compared with
+    the same boxes integrated one after another through the single-box path."""
+    boxes = W.config5(nboxes)
+    ntot = sum(s.n for s in boxes)
+    log(f"ensemble: {nboxes} boxes, {ntot} particles")
+    ens = lj.Ensemble(boxes)
+    w, blk = ens.tune(dt, 10)
+    ens.run(dt, 0)                   # initial forces
+    ens.run(dt, 10)                  # warm-up, capture
+    ens.pairs()
+    t0 = time.perf_counter()
+    ens.run(dt, steps, use_graph=True)
+    t_ens = time.perf_counter() - t0
+    pairs = ens.pairs()
+    graph = ens.uses_graph()
+    ens.close()
+    seq = list(range(len(boxes))) if seq_boxes is None else list(seq_boxes)
+    t_seq, n_seq = 0.0, 0
+    cfg = lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, w)
+    for k in seq:
+        s = boxes[k]
+        if int(np.floor(s.L / s.rc)) < 3:
+            continue                 # the single-box path needs >= 3 cells per axis
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos, s.vel)
+        d.integrate(dt, 1, cfg)
+        d.counters()
+        t0 = time.perf_counter()
+        d.integrate(dt, steps, cfg)
+        d.counters()
+        t_seq += time.perf_counter() - t0
+        n_seq += s.n
+        d.close()
+    out = {"boxes": nboxes, "particles": ntot, "steps": steps, "w": w, "block": blk, "graph": graph,
+           "ensemble_s": t_ens, "pairs_per_s": pairs / t_ens, "particle_steps_per_s": ntot * steps / t_ens,
+           "sequential_s": t_seq, "sequential_particles": n_seq,
+           "sequential_particle_steps_per_s": n_seq * steps / t_seq if t_seq else None}
+    if t_seq:
+        out["speedup_vs_sequential"] = out["particle_steps_per_s"] / out["sequential_particle_steps_per_s"]
+    log(json.dumps(out))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["sweep", "train", "droplet"])
+    ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--data", default="gpurun_out/tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
@@ -171,6 +220,10 @@ def main(argv=None):
             print(json.dumps({k: v for k, v in summ.items() if k != "rows"}))
             if a.out:
                 json.dump(summ, open(a.out, "w"))
+    elif a.what == "ensemble":
+        res = ensemble(steps=a.steps)
+        if a.out:
+            json.dump(res, open(a.out, "w"))
     else:
         res = droplet(a.radius, a.steps, a.phase, model_path=a.model)
         print(json.dumps({k: v for k, v in res.items() if k != "evidence"}))

@@ -100,6 +100,7 @@ _SIGS = {
     "lj_ensemble_size": (C.c_int64, [_VP]),
     "lj_ensemble_uses_graph": (C.c_int32, [_VP]),
     "lj_ensemble_last_error": (C.c_char_p, [_VP]),
+    "lj_ensemble_pairs": (C.c_int64, [_VP]),
     "lj_ensemble_destroy": (None, [_VP]),
     "lj_last_error": (C.c_char_p, [_VP]),
     "lj_destroy": (None, [_VP]),
@@ -356,6 +357,10 @@ class Ensemble:
 
     def last_error(self):
         return self.lib.lj_ensemble_last_error(self.h).decode()
+
+    def pairs(self):
+        """Unique in-cutoff pairs over the force evaluations since the last call."""
+        return int(self.lib.lj_ensemble_pairs(self.h))
 
     def debug(self, spin_limit=0, skip_block=-1):
         self.lib.lj_ensemble_debug(self.h, spin_limit, skip_block)
