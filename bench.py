@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1048576)
+    ap.add_argument("--particles", type=int, default=1048576)
     ap.add_argument("--tune", default="learned", choices=["learned", "full", "fixed"])
     ap.add_argument("--cfg", default=None, help="fixed configuration, e.g. 1,5,0,1 (container,order,param,n3)")
     ap.add_argument("--samples", type=int, default=3)
@@ -127,6 +127,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def reduce_over_ranks(pg, seconds, pairs, device=None):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the sum of all ranks' pairs (no data-path collective; timing only)."""
+    if not pg:
+        return float(seconds), float(pairs)
+    import torch
+    t = torch.tensor([seconds, pairs], dtype=torch.float64, device=device)
+    tmax, tsum = t.clone(), t.clone()
+    pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+    pg.all_reduce(tsum, op=pg.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def traffic_from_profiles(cfg_name):
     """DRAM bytes per force-kernel launch from the committed ncu summary, if it
     was taken for this configuration (line: 'traffic <config> <bytes>')."""
@@ -158,7 +171,7 @@ def run_reference(args, ws, rank, pg):
     from paper_2512_03565_gb300 import workloads as W
     if rank != 0:
         return 0
-    s = W.config2(args.n)
+    s = W.config2(args.particles)
     for _ in range(args.warmup):
         cpu_oracle_rate(s, evals_max=1)
     times, pairs = [], []
@@ -195,7 +208,7 @@ def run_ours(args, ws, rank, local, pg):
     stream = torch.cuda.current_stream(dev)
 
     # replica per rank: same workload shape, rank-specific seed
-    s = W.homogeneous(args.n, 0.75, W.BASE_SEED + 1 + 7919 * rank, T=1.0, rc=2.5, skin=0.3)
+    s = W.homogeneous(args.particles, 0.75, W.BASE_SEED + 1 + 7919 * rank, T=1.0, rc=2.5, skin=0.3)
     pos_d = torch.from_numpy(s.pos.view(np.int32)).to(dev)
     vel_d = torch.from_numpy(s.vel).to(dev)
     d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP32_ACC64, stream=stream)
@@ -253,15 +266,7 @@ def run_ours(args, ws, rank, local, pg):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
     my_pairs = float(sum(pairs))
-    if pg:
-        t = torch.tensor([total_s, my_pairs], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        tsum = t.clone()
-        pg.all_reduce(tsum, op=pg.ReduceOp.SUM)
-        total_s_all, pairs_all = float(tmax[0]), float(tsum[1])
-    else:
-        total_s_all, pairs_all = total_s, my_pairs
+    total_s_all, pairs_all = reduce_over_ranks(pg, total_s, my_pairs, dev)
     value = pairs_all / total_s_all
 
     # roofline of the dominant kernel (the force kernel): useful FP32 flops of

@@ -161,9 +161,11 @@ def test_quantization_matches_oracle(lj):
     d.close()
 
 
-def test_integrator_matches_oracle_fp64(lj):
+@pytest.mark.parametrize("cfg_args", [(0, 3, 8, 0), (1, 5, 0, 0), (1, 3, 4, 0), (1, 5, 0, 1)],
+                         ids=["LC-JSPLIT8", "VL-IPT", "VL-JSPLIT4", "VL-IPT-N3"])
+def test_integrator_matches_oracle_fp64(lj, cfg_args):
     s = W.stratified(3000, 0.7, 12, T=1.0)
-    cfg = lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, 8)
+    cfg = lj.config(*cfg_args)
     d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
     d.set_particles(s.pos, s.vel)
     d.integrate(0.002, 20, cfg)
