@@ -231,7 +231,10 @@ lj_status lj_get_verlet(lj_ctx* ctx, int32_t* nbr, int32_t* nnbr, int32_t* cap_o
 
 /* Counters since the context was created: cnt[0] = force evaluations,
  * cnt[1] = unique in-cutoff pairs of the last evaluation, cnt[2] = list builds,
- * cnt[3] = early (skin) rebuilds, cnt[4] = capacity regrowths. */
+ * cnt[3] = early (skin) rebuilds, cnt[4] = capacity regrowths.  In
+ * lj_integrate_step the force of a step without a scheduled rebuild starts
+ * before the skin check is read back; a step that then needs an early rebuild
+ * evaluates the forces twice and cnt[0] counts both. */
 lj_status lj_get_counters(lj_ctx* ctx, int64_t* cnt5);
 
 /* Force-kernel timing with CUDA events recorded on the context's stream

@@ -315,8 +315,7 @@ int force_launches(const Ctx& c, const lj_config& cfg, bool tiles_rebuilt) {
 }
 
 lj_status run_force(Ctx& c, const lj_config& cfg, bool ev) {
-  CK(cudaMemsetAsync(c.ev, 0, 2 * sizeof(double), c.stream));
-  CK(cudaMemsetAsync(c.npairs, 0, sizeof(unsigned long long), c.stream));
+  CK(cudaMemsetAsync(c.ev, 0, 2 * sizeof(double) + sizeof(unsigned long long), c.stream));  // ev and npairs
   c.P.n = (int32_t)c.n;
   cudaError_t e;
   const bool f64 = c.prec == LJ_PREC_FP64;
@@ -420,8 +419,9 @@ lj_status lj_init_domain(lj_ctx** out, const double box[3], double cutoff, doubl
   P.e24 = 24.0 * eps;
   P.e4 = 4.0 * eps;
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&c.ev, 2 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c.npairs, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c.ev, 3 * sizeof(double));
+  if (e == cudaSuccess) c.npairs = reinterpret_cast<unsigned long long*>(c.ev + 2);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.status_copied, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&c.status, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c.maxlen, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c.tile_ctr, sizeof(uint32_t));
@@ -564,9 +564,18 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
     c.moved_since_build = true;
     if (vl) {
       c.steps_since_build += 1;
-      bool rebuild = c.steps_since_build >= rebuild_every || !c.vl_valid;
-      if (!rebuild) {
-        CKS(sync_status(c));
+      const bool scheduled = c.steps_since_build >= rebuild_every || !c.vl_valid;
+      bool rebuild = scheduled;
+      if (!scheduled) {
+        // The drift's skin flag comes back while the force kernel already runs
+        // on the current lists, so the host's wait overlaps GPU work.  If a
+        // particle left its skin the lists are rebuilt and the forces computed
+        // again, replacing the speculative ones (and any status they raised).
+        CK(cudaMemcpyAsync(c.host_status, c.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaEventRecord(c.status_copied, c.stream));
+        c.P.nc = c.nc_vl;
+        CKS(run_force(c, cfg, false));
+        CK(cudaEventSynchronize(c.status_copied));
         if (*c.host_status & ST_SKIN) {
           CK(cudaMemsetAsync(c.status, 0, sizeof(uint32_t), c.stream));
           rebuild = true;
@@ -577,13 +586,14 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
         CKS(do_build_verlet(c, cfg.newton3 != LJ_N3_OFF ? 1 : 0, cfg.order == LJ_ORD_VL_IPT ? 1 : 0,
                             cfg.newton3 == LJ_N3_TWOPASS));
         c.moved_since_build = false;
+        c.P.nc = c.nc_vl;
+        CKS(run_force(c, cfg, false));
       }
-      c.P.nc = c.nc_vl;
     } else {
       CKS(do_bin(c, LJ_LC));
       c.P.nc = c.nc_lc;
+      CKS(run_force(c, cfg, false));
     }
-    CKS(run_force(c, cfg, false));
     CK(launch_kick_drift(c, hdtm, dtu, true, false));
   }
   CK(cudaMemcpyAsync(c.host_np, c.npairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.stream));
@@ -819,13 +829,14 @@ void lj_destroy(lj_ctx* h) {
   cudaStreamSynchronize(c.stream);
   void* dev[] = {c.pos, c.pos_alt, c.vel, c.vel_alt, c.frc, c.frc_alt, c.cell_start, c.cnt, c.cell_of, c.slot,
                  c.key, c.scan_tmp, c.tiles, c.row_tiles, c.nbr, c.nnbr, c.x_build, c.maxlen, c.twopass,
-                 c.rev_cnt, c.rev_start, c.rev_slot, c.rev_key, c.rev_key2, c.ev, c.npairs, c.status,
+                 c.rev_cnt, c.rev_start, c.rev_slot, c.rev_key, c.rev_key2, c.ev, c.status,
                  c.feat_stats, c.tile_ctr, c.stage, c.nbr16};
   for (void* p : dev) dfree(p);
   if (c.host_ev) cudaFreeHost(c.host_ev);
   if (c.host_np) cudaFreeHost(c.host_np);
   if (c.host_status) cudaFreeHost(c.host_status);
   for (cudaEvent_t e : c.ev_pool) cudaEventDestroy(e);
+  if (c.status_copied) cudaEventDestroy(c.status_copied);
   delete h;
 }
 

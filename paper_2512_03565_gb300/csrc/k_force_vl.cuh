@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
 }
 
 template <typename R, int W, int N3, bool EV, bool I16>
-__global__ void __launch_bounds__(256) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
+__global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
   constexpr int G = 32 / W;
   const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
   const int64_t n = P.n;

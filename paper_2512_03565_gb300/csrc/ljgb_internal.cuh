@@ -359,12 +359,13 @@ struct Ctx {
   uint32_t* maxlen = nullptr;     // device: longest list of the last build
 
   // accumulators and status
-  double* ev = nullptr;    // 2 doubles
-  unsigned long long* npairs = nullptr;
+  double* ev = nullptr;    // 2 doubles, then the pair counter (one allocation, cleared by one memset)
+  unsigned long long* npairs = nullptr;  // = (unsigned long long*)(ev + 2)
   uint32_t* status = nullptr;
   double* host_ev = nullptr;  // pinned mirror
   unsigned long long* host_np = nullptr;
   uint32_t* host_status = nullptr;
+  cudaEvent_t status_copied = nullptr;  // recorded after a status read-back
 
   // L2 persisting window over the positions for the Verlet-list kernels (0 = off)
   size_t l2_window_bytes = 0;

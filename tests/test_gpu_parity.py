@@ -148,6 +148,30 @@ def test_edge_cases_fp64(lj, name, L, pos):
     d.close()
 
 
+@pytest.mark.parametrize("name,L,pos", [c for c in edge_cases() if c[0] in ("uniform", "crowded_cell", "faces")][:3] +
+                         [c for c in edge_cases() if c[0] == "crowded_cell"],
+                         ids=["uniform-nc3", "uniform-nc4", "uniform-nc5", "crowded_cell"])
+def test_verlet_lists_bit_exact_edge(lj, name, L, pos):
+    """Lists on 3-5 cells per axis (at 3 one segment covers a whole row of
+    cells and takes the integer path) and on a 300-particle cell, whose lists
+    outgrow the builder's shared staging and take its direct-store path:
+    entries, lengths and scan order equal the oracle's for full and half lists."""
+    rl = 1.0
+    d = lj.Domain(L, rl, 0.0, precision=lj.LJ_PREC_FP64)
+    d.set_particles(pos)
+    nc = oracle.ncells(L, rl)
+    for half in (0, 1):
+        d.build_verlet(half)
+        nbr, nn = d.verlet()
+        _, _, nbr_ref, nn_ref, _ = oracle.verlet(pos, L, rl, nc, half, nbr.shape[1])
+        assert np.array_equal(nn, nn_ref)
+        for i in range(pos.shape[1]):
+            assert np.array_equal(nbr[i, :nn[i]], nbr_ref[i, :nn[i]]), (name, half, i)
+    if name == "crowded_cell":
+        assert nn.max() > 64
+    d.close()
+
+
 def test_quantization_matches_oracle(lj):
     rng = np.random.default_rng(5)
     L = 12.345
