@@ -225,6 +225,10 @@ lj_status do_build_verlet(Ctx& c, int half, int colmajor, bool twopass) {
     c.counters[4] += 1;
     if (attempt == 3) return fail(c, LJ_ERR_CAPACITY, "Verlet list capacity could not be grown");
   }
+  if (*c.host_status & ST_SKIN) {  // a fresh list makes an earlier skin flag stale
+    *c.host_status &= ~ST_SKIN;
+    CK(cudaMemcpyAsync(c.status, c.host_status, sizeof(uint32_t), cudaMemcpyHostToDevice, c.stream));
+  }
   c.vl_half = half;
   c.vl_colmajor = colmajor;
   // 16-bit copy of the lists (halves the list bytes) when every entry
@@ -314,8 +318,9 @@ int force_launches(const Ctx& c, const lj_config& cfg, bool tiles_rebuilt) {
   return 1 + (tiles_rebuilt ? 5 : 0);
 }
 
-lj_status run_force(Ctx& c, const lj_config& cfg, bool ev) {
-  CK(cudaMemsetAsync(c.ev, 0, 2 * sizeof(double) + sizeof(unsigned long long), c.stream));  // ev and npairs
+lj_status run_force(Ctx& c, const lj_config& cfg, bool ev, bool acc_zeroed = false) {
+  if (!acc_zeroed)  // energy, virial and pair counter
+    CK(cudaMemsetAsync(c.ev, 0, 2 * sizeof(double) + sizeof(unsigned long long), c.stream));
   c.P.n = (int32_t)c.n;
   cudaError_t e;
   const bool f64 = c.prec == LJ_PREC_FP64;
@@ -421,7 +426,9 @@ lj_status lj_init_domain(lj_ctx** out, const double box[3], double cutoff, doubl
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&c.ev, 3 * sizeof(double));
   if (e == cudaSuccess) c.npairs = reinterpret_cast<unsigned long long*>(c.ev + 2);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.status_copied, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.drift_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaHostAlloc(&c.skin_host, sizeof(uint32_t), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c.skin_dev, c.skin_host, 0);
   if (e == cudaSuccess) e = cudaMalloc(&c.status, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c.maxlen, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c.tile_ctr, sizeof(uint32_t));
@@ -558,7 +565,11 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
     c.last_cfg = cfg;
   }
   for (int s = 0; s < nsteps; ++s) {
-    CK(launch_kick_drift(c, hdtm, dtu, false, vl && c.vl_valid));
+    const bool track = vl && c.vl_valid;
+    const bool speculate = track && c.steps_since_build + 1 < rebuild_every;
+    if (speculate) *reinterpret_cast<volatile uint32_t*>(c.skin_host) = 0u;
+    CK(launch_kick_drift(c, hdtm, dtu, false, track, speculate ? c.skin_dev : nullptr,
+                         speculate ? c.ev : nullptr));
     c.launches += 2;  // kick-drift now, the closing kick below
     c.moved = true;
     c.moved_since_build = true;
@@ -567,16 +578,17 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
       const bool scheduled = c.steps_since_build >= rebuild_every || !c.vl_valid;
       bool rebuild = scheduled;
       if (!scheduled) {
-        // The drift's skin flag comes back while the force kernel already runs
-        // on the current lists, so the host's wait overlaps GPU work.  If a
-        // particle left its skin the lists are rebuilt and the forces computed
-        // again, replacing the speculative ones (and any status they raised).
-        CK(cudaMemcpyAsync(c.host_status, c.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
-        CK(cudaEventRecord(c.status_copied, c.stream));
+        // The drift writes its skin flag to mapped host memory and the force
+        // kernel is queued at once on the current lists (the drift kernel also
+        // cleared its accumulators), so the host's wait for the flag overlaps
+        // GPU work.  If a particle left its skin the lists are rebuilt and the
+        // forces computed again, replacing the speculative ones (and any
+        // status they raised).
+        CK(cudaEventRecord(c.drift_done, c.stream));
         c.P.nc = c.nc_vl;
-        CKS(run_force(c, cfg, false));
-        CK(cudaEventSynchronize(c.status_copied));
-        if (*c.host_status & ST_SKIN) {
+        CKS(run_force(c, cfg, false, true));
+        CK(cudaEventSynchronize(c.drift_done));
+        if (*reinterpret_cast<volatile uint32_t*>(c.skin_host)) {
           CK(cudaMemsetAsync(c.status, 0, sizeof(uint32_t), c.stream));
           rebuild = true;
           c.counters[3] += 1;
@@ -836,7 +848,8 @@ void lj_destroy(lj_ctx* h) {
   if (c.host_np) cudaFreeHost(c.host_np);
   if (c.host_status) cudaFreeHost(c.host_status);
   for (cudaEvent_t e : c.ev_pool) cudaEventDestroy(e);
-  if (c.status_copied) cudaEventDestroy(c.status_copied);
+  if (c.drift_done) cudaEventDestroy(c.drift_done);
+  if (c.skin_host) cudaFreeHost(c.skin_host);
   delete h;
 }
 

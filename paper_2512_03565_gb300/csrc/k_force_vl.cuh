@@ -147,25 +147,35 @@ __global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, Forc
     if (vi) {
       const uint4 pi = A.pos[i];
       const int m = min(A.nnbr[i], A.cap);
-      const int64_t row = i * A.cap;
+      // running pointer to this lane's next entries of row i (entries k0 + t W)
+      const int32_t* rp = A.nbr + i * A.cap + sub;
+      const int16_t* rp16 = I16 ? A.nbr16 + i * A.cap + sub : nullptr;
+      auto entry = [&](int off) -> int {
+        if (I16) {
+          int64_t j = i + (int64_t)__ldcs(rp16 + off);
+          j += (j < 0) ? n : 0;
+          j -= (j >= n) ? n : 0;
+          return (int)j;
+        }
+        return __ldcs(rp + off);
+      };
       int jc[VL_BATCH];
 #pragma unroll
-      for (int t = 0; t < VL_BATCH; ++t) jc[t] = (sub + t * W < m) ? vl_entry<I16>(A, row + sub + t * W, i, n) : (int)i;
+      for (int t = 0; t < VL_BATCH; ++t) jc[t] = (sub + t * W < m) ? entry(t * W) : (int)i;
       for (int k0 = sub; k0 < m; k0 += W * VL_BATCH) {
         uint4 pj[VL_BATCH];
 #pragma unroll
         for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jc[t]);
         int jn[VL_BATCH];
+        rp += W * VL_BATCH;
+        if (I16) rp16 += W * VL_BATCH;
 #pragma unroll
-        for (int t = 0; t < VL_BATCH; ++t) {
-          const int k = k0 + W * VL_BATCH + t * W;
-          jn[t] = (k < m) ? vl_entry<I16>(A, row + k, i, n) : (int)i;
-        }
+        for (int t = 0; t < VL_BATCH; ++t) jn[t] = (k0 + W * VL_BATCH + t * W < m) ? entry(t * W) : (int)i;
 #pragma unroll
         for (int t = 0; t < VL_BATCH; ++t) {
           R af, bf, cf;
-          const R fac = Prec<R>::template pair<EV>(mimg(pi.x, pj[t].x), mimg(pi.y, pj[t].y), mimg(pi.z, pj[t].z), P,
-                                                   af, bf, cf, eu, ew, cnt);
+          const R fac = Prec<R>::template pair<EV, false, true>(mimg(pi.x, pj[t].x), mimg(pi.y, pj[t].y),
+                                                                mimg(pi.z, pj[t].z), P, af, bf, cf, eu, ew, cnt);
           fx += fac * af;
           fy += fac * bf;
           fz += fac * cf;

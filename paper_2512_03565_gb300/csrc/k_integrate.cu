@@ -11,11 +11,19 @@ static inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t)
 // where rne(v * dtu) is the exact product rounded once to the nearest integer:
 // fma(v, dtu, 1.5 * 2^52) lies in [2^52, 2^53) where the spacing is 1, and its
 // low 32 bits are the displacement modulo 2^32.  With track, particles whose
-// displacement since the last list build exceeds skin/2 set ST_SKIN.
+// displacement since the last list build exceeds skin/2 set ST_SKIN (and the
+// mapped host word skin_flag, when given).  zero_acc, when given, is cleared
+// (two doubles and a counter) for the force evaluation queued next.
 __global__ void k_kick_drift(uint4* __restrict__ pos, double* __restrict__ vel, const double* __restrict__ frc,
                              int64_t n, double hdtm, double dtu, int drift, const uint32_t* __restrict__ xb,
-                             uint64_t disp2_max, uint32_t* __restrict__ status) {
+                             uint64_t disp2_max, uint32_t* __restrict__ status, uint32_t* skin_flag,
+                             double* __restrict__ zero_acc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (zero_acc && i == 0) {  // energy, virial and pair counter of the force evaluation that follows
+    zero_acc[0] = 0.0;
+    zero_acc[1] = 0.0;
+    reinterpret_cast<unsigned long long*>(zero_acc)[2] = 0ull;
+  }
   if (i >= n) return;
   double v0 = __fma_rn(hdtm, frc[i], vel[i]);
   double v1 = __fma_rn(hdtm, frc[n + i], vel[n + i]);
@@ -33,16 +41,21 @@ __global__ void k_kick_drift(uint4* __restrict__ pos, double* __restrict__ vel, 
   if (xb) {
     const int a = (int)(p.x - xb[i]), b = (int)(p.y - xb[n + i]), c = (int)(p.z - xb[2 * n + i]);
     const uint64_t d2 = (uint64_t)((long long)a * a) + (uint64_t)((long long)b * b) + (uint64_t)((long long)c * c);
-    if (d2 > disp2_max) atomicOr(status, ST_SKIN);
+    if (d2 > disp2_max) {
+      atomicOr(status, ST_SKIN);
+      if (skin_flag) *skin_flag = 1u;  // mapped host word: any writer sets it
+    }
   }
 }
 
-cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track) {
+cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track, uint32_t* skin_flag,
+                              double* zero_acc) {
   const double half_skin_u = 0.5 * c.skin * 4294967296.0 / c.L;
   const double d2 = half_skin_u * half_skin_u;
   const uint64_t d2max = d2 >= 1.8e19 ? ~0ull : (uint64_t)d2;
   k_kick_drift<<<nb(c.n, 256), 256, 0, c.stream>>>(c.pos, c.vel, c.frc, c.n, hdtm, dtu, kick_only ? 0 : 1,
-                                                   track ? c.x_build : nullptr, d2max, c.status);
+                                                   track ? c.x_build : nullptr, d2max, c.status, skin_flag,
+                                                   zero_acc);
   return cudaGetLastError();
 }
 

@@ -139,35 +139,44 @@ __device__ __forceinline__ float coarse_r2(int a, int b, int c) {
   return fmaf(z, z, fmaf(y, y, x * x));
 }
 
-template <bool EV, bool SCREEN = false>
+// SELECT evaluates the pair unconditionally and selects the result, so the
+// warp takes no branch (for list orders where most entries are inside and the
+// branch is always taken by some lane); otherwise a pair outside the cutoff
+// returns early, and SCREEN first rejects candidates by the coarse r^2.
+template <bool EV, bool SCREEN = false, bool SELECT = false>
 __device__ __forceinline__ float pair_f32(int a, int b, int c, const LJParams& P, float& af, float& bf,
                                           float& cf, float& eu, float& ew, int& cnt) {
-  af = bf = cf = 0.0f;
   if (SCREEN) {
     const float r2p = coarse_r2(a, b, c);
-    if (r2p > P.rc2p_hi) return 0.0f;  // certainly outside the cutoff
+    if (r2p > P.rc2p_hi) {  // certainly outside the cutoff
+      af = bf = cf = 0.0f;
+      return 0.0f;
+    }
   }
   const uint64_t R2 = r2_exact(a, b, c);
-  float fac = 0.0f;
-  if (R2 - 1ull < P.Rc2) {  // 0 < R2 <= Rc2 (R2 = 0 wraps to the largest value)
-    af = __int2float_rn(a);
-    bf = __int2float_rn(b);
-    cf = __int2float_rn(c);
-    // R2 to FP32 from its two 32-bit words: 64-bit conversions run on the FP64
-    // pipe (1/80 rate on GB300); the high word is below 2^24 whenever
-    // r_c < L/16, so the sum carries a single rounding
-    const float r2 = fmaf(__uint2float_rn((uint32_t)(R2 >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)R2));
-    const float inv = rcp_nr(r2);
-    const float s2 = fmaf(inv, P.S_hi, inv * P.S_lo);
-    const float s6 = s2 * s2 * s2;
-    const float t = fmaf(2.0f, s6, -1.0f);
-    fac = s6 * t * inv;
-    if (EV) {
-      eu += fmaf(s6, s6, -s6);
-      ew += s6 * t;
-    }
-    cnt += 1;
+  const bool in = R2 - 1ull < P.Rc2;  // 0 < R2 <= Rc2 (R2 = 0 wraps to the largest value)
+  if (!SELECT && !in) {
+    af = bf = cf = 0.0f;
+    return 0.0f;
   }
+  // R2 to FP32 from its two 32-bit words: 64-bit conversions run on the FP64
+  // pipe (1/80 rate on GB300); the high word is below 2^24 whenever r_c < L/16,
+  // so the sum carries a single rounding
+  const float r2 = fmaf(__uint2float_rn((uint32_t)(R2 >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)R2));
+  af = __int2float_rn(a);
+  bf = __int2float_rn(b);
+  cf = __int2float_rn(c);
+  const float inv = rcp_nr(r2);
+  const float s2 = fmaf(inv, P.S_hi, inv * P.S_lo);
+  const float s6 = s2 * s2 * s2;
+  const float t = fmaf(2.0f, s6, -1.0f);
+  const bool keep = SELECT ? in : true;
+  const float fac = keep ? s6 * t * inv : 0.0f;
+  if (EV) {
+    eu += keep ? fmaf(s6, s6, -s6) : 0.0f;
+    ew += keep ? s6 * t : 0.0f;
+  }
+  cnt += keep ? 1 : 0;
   return fac;
 }
 
@@ -201,16 +210,16 @@ template <typename R>
 struct Prec;
 template <>
 struct Prec<float> {
-  template <bool EV, bool SCREEN = false>
+  template <bool EV, bool SCREEN = false, bool SELECT = false>
   __device__ __forceinline__ static float pair(int a, int b, int c, const LJParams& P, float& af, float& bf,
                                                float& cf, float& eu, float& ew, int& cnt) {
-    return pair_f32<EV, SCREEN>(a, b, c, P, af, bf, cf, eu, ew, cnt);
+    return pair_f32<EV, SCREEN, SELECT>(a, b, c, P, af, bf, cf, eu, ew, cnt);
   }
   __device__ __forceinline__ static double to_d(float v) { return f2d_exact(v); }
 };
 template <>
 struct Prec<double> {
-  template <bool EV, bool SCREEN = false>
+  template <bool EV, bool SCREEN = false, bool SELECT = false>
   __device__ __forceinline__ static double pair(int a, int b, int c, const LJParams& P, double& ad,
                                                 double& bd, double& cd, double& eu, double& ew, int& cnt) {
     return pair_f64<EV>(a, b, c, P, ad, bd, cd, eu, ew, cnt);
@@ -365,7 +374,11 @@ struct Ctx {
   double* host_ev = nullptr;  // pinned mirror
   unsigned long long* host_np = nullptr;
   uint32_t* host_status = nullptr;
-  cudaEvent_t status_copied = nullptr;  // recorded after a status read-back
+  // skin flag of the integrator's drift in mapped pinned memory (host view and
+  // device alias): the drift kernel writes it, the host reads it after an event
+  uint32_t* skin_host = nullptr;
+  uint32_t* skin_dev = nullptr;
+  cudaEvent_t drift_done = nullptr;
 
   // L2 persisting window over the positions for the Verlet-list kernels (0 = off)
   size_t l2_window_bytes = 0;
@@ -424,7 +437,8 @@ cudaError_t force_lc_f32(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t force_lc_f64(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t force_vl_f32(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t force_vl_f64(Ctx& c, const lj_config& cfg, bool ev);
-cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track);
+cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track,
+                              uint32_t* skin_flag = nullptr, double* zero_acc = nullptr);
 cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s);
 cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s);
 cudaError_t launch_feature_stats(Ctx& c, unsigned long long* stats);

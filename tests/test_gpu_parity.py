@@ -303,8 +303,18 @@ def test_capacity_regrowth_and_skin_rebuild(lj):
     vel[:, 0] = [2000.0, 0.0, 0.0]                # moves 4 sigma in one step of dt = 0.002
     d2 = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
     d2.set_particles(pos, vel)
-    d2.integrate(0.002, 3, cfg, rebuild_every=1000)
+    d2.integrate(0.002, 1, cfg, rebuild_every=1000)
     assert d2.counters()[3] >= 1                  # early (skin) rebuild counted
+    # the closing kick of the skin step used the forces of the rebuilt lists:
+    # the step equals the oracle's velocity Verlet (no lists) to FP64 rounding.
+    # (Later steps are not compared: the teleported particle then nearly hits
+    # another, |F| ~ 1e12, and rounding decides the trajectory.)
+    p1, v1 = d2.state()
+    p_ref, v_ref, _, _, _ = oracle.vv_run(pos, vel, s.L, s.rc, 1.0, 0.002, 1, use_cells=True)
+    dp = np.abs(p1.astype(np.int64) - p_ref.astype(np.int64))
+    assert np.minimum(dp, 2 ** 32 - dp).max() <= 2
+    assert np.abs(v1 - v_ref).max() <= 1e-9 * np.abs(v_ref).max()
+    d2.integrate(0.002, 2, cfg, rebuild_every=1000)
     p2, _ = d2.state()
     d2.compute_forces(cfg)
     F_ref, _, _, _ = oracle.forces_bruteforce(p2, s.L, s.rc)
