@@ -151,7 +151,10 @@ int32_t lj_config_list(lj_config* out, int32_t cap);
  * point, rounded to nearest, periodic wrap); F = F(x) with cfg; v += dt/(2m) F.
  * Verlet lists are rebuilt every rebuild_every steps (and early when a particle
  * moved more than skin/2).  Computes the initial forces if none are current.
- * Errors: as lj_compute_forces. */
+ * The last step's closing half kick is kept pending on the device and applied
+ * by the next call's first kick (as a separate FMA, so the arithmetic is that
+ * of unfused kicks), or first thing by lj_get_state, lj_kinetic_energy and any
+ * force evaluation; lj_set_particles drops it.  Errors: as lj_compute_forces. */
 lj_status lj_integrate_step(lj_ctx* ctx, double dt, int32_t nsteps, int32_t rebuild_every,
                             lj_config cfg);
 

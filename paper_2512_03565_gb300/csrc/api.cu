@@ -169,6 +169,7 @@ lj_status alloc_particles(Ctx& c, int64_t n) {
 }
 
 void reset_state_flags(Ctx& c) {
+  c.kick_pending = false;  // new particles: nothing of the last step is due
   c.binned_nc = 0;
   c.binned_for = -1;
   c.vl_valid = false;
@@ -318,7 +319,19 @@ int force_launches(const Ctx& c, const lj_config& cfg, bool tiles_rebuilt) {
   return 1 + (tiles_rebuilt ? 5 : 0);
 }
 
+// Applies the pending closing half kick of the last integrated step (with the
+// forces it was due with); every reader of velocities and every recomputation
+// of the forces comes here first.
+lj_status settle_kick(Ctx& c) {
+  if (!c.kick_pending) return LJ_OK;
+  CK(launch_kick_drift(c, c.kick_hdtm, 0.0, true, false));
+  c.kick_pending = false;
+  c.launches += 1;
+  return LJ_OK;
+}
+
 lj_status run_force(Ctx& c, const lj_config& cfg, bool ev, bool acc_zeroed = false) {
+  CKS(settle_kick(c));
   if (!acc_zeroed)  // energy, virial and pair counter
     CK(cudaMemsetAsync(c.ev, 0, 2 * sizeof(double) + sizeof(unsigned long long), c.stream));
   c.P.n = (int32_t)c.n;
@@ -564,13 +577,17 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
     CKS(run_force(c, cfg, false));
     c.last_cfg = cfg;
   }
+  // Each step's closing half kick is left pending and fused into the next
+  // step's first kick (the next call's, or lj_get_state / lj_kinetic_energy /
+  // a force evaluation apply it on their own): one kernel per step less.
   for (int s = 0; s < nsteps; ++s) {
     const bool track = vl && c.vl_valid;
     const bool speculate = track && c.steps_since_build + 1 < rebuild_every;
     if (speculate) *reinterpret_cast<volatile uint32_t*>(c.skin_host) = 0u;
     CK(launch_kick_drift(c, hdtm, dtu, false, track, speculate ? c.skin_dev : nullptr,
-                         speculate ? c.ev : nullptr));
-    c.launches += 2;  // kick-drift now, the closing kick below
+                         speculate ? c.ev : nullptr, c.kick_pending, c.kick_hdtm));
+    c.kick_pending = false;
+    c.launches += 1;
     c.moved = true;
     c.moved_since_build = true;
     if (vl) {
@@ -606,7 +623,8 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
       c.P.nc = c.nc_lc;
       CKS(run_force(c, cfg, false));
     }
-    CK(launch_kick_drift(c, hdtm, dtu, true, false));
+    c.kick_pending = true;
+    c.kick_hdtm = hdtm;
   }
   CK(cudaMemcpyAsync(c.host_np, c.npairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.stream));
   c.np_side = cfg.newton3 == LJ_N3_OFF ? 0.5 : 1.0;
@@ -632,6 +650,7 @@ lj_status lj_get_state(lj_ctx* h, uint32_t* pos_fp, double* vel, int32_t on_devi
   if (!h) return LJ_ERR_ARG;
   Ctx& c = h->c;
   CKS(need_particles(c));
+  CKS(settle_kick(c));
   const size_t n = (size_t)c.n;
   if (pos_fp) {
     if (on_device) {
@@ -789,6 +808,7 @@ lj_status lj_kinetic_energy(lj_ctx* h, double* ke) {
   if (!h || !ke) return LJ_ERR_ARG;
   Ctx& c = h->c;
   CKS(need_particles(c));
+  CKS(settle_kick(c));
   CK(launch_ke(c, c.ev));
   CK(cudaMemcpyAsync(c.host_ev, c.ev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));

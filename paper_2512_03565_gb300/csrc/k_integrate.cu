@@ -13,11 +13,13 @@ static inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t)
 // low 32 bits are the displacement modulo 2^32.  With track, particles whose
 // displacement since the last list build exceeds skin/2 set ST_SKIN (and the
 // mapped host word skin_flag, when given).  zero_acc, when given, is cleared
-// (two doubles and a counter) for the force evaluation queued next.
+// (two doubles and a counter) for the force evaluation queued next.  With pre,
+// the previous step's closing half kick (hpre) is applied first, as its own
+// rounded FMA, so that fusing the two kicks leaves the arithmetic unchanged.
 __global__ void k_kick_drift(uint4* __restrict__ pos, double* __restrict__ vel, const double* __restrict__ frc,
                              int64_t n, double hdtm, double dtu, int drift, const uint32_t* __restrict__ xb,
                              uint64_t disp2_max, uint32_t* __restrict__ status, uint32_t* skin_flag,
-                             double* __restrict__ zero_acc) {
+                             double* __restrict__ zero_acc, int pre, double hpre) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (zero_acc && i == 0) {  // energy, virial and pair counter of the force evaluation that follows
     zero_acc[0] = 0.0;
@@ -25,9 +27,16 @@ __global__ void k_kick_drift(uint4* __restrict__ pos, double* __restrict__ vel, 
     reinterpret_cast<unsigned long long*>(zero_acc)[2] = 0ull;
   }
   if (i >= n) return;
-  double v0 = __fma_rn(hdtm, frc[i], vel[i]);
-  double v1 = __fma_rn(hdtm, frc[n + i], vel[n + i]);
-  double v2 = __fma_rn(hdtm, frc[2 * n + i], vel[2 * n + i]);
+  const double f0 = frc[i], f1 = frc[n + i], f2 = frc[2 * n + i];
+  double v0 = vel[i], v1 = vel[n + i], v2 = vel[2 * n + i];
+  if (pre) {  // the previous step's closing half kick, then this step's first
+    v0 = __fma_rn(hpre, f0, v0);
+    v1 = __fma_rn(hpre, f1, v1);
+    v2 = __fma_rn(hpre, f2, v2);
+  }
+  v0 = __fma_rn(hdtm, f0, v0);
+  v1 = __fma_rn(hdtm, f1, v1);
+  v2 = __fma_rn(hdtm, f2, v2);
   vel[i] = v0;
   vel[n + i] = v1;
   vel[2 * n + i] = v2;
@@ -49,13 +58,13 @@ __global__ void k_kick_drift(uint4* __restrict__ pos, double* __restrict__ vel, 
 }
 
 cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track, uint32_t* skin_flag,
-                              double* zero_acc) {
+                              double* zero_acc, bool pre, double hpre) {
   const double half_skin_u = 0.5 * c.skin * 4294967296.0 / c.L;
   const double d2 = half_skin_u * half_skin_u;
   const uint64_t d2max = d2 >= 1.8e19 ? ~0ull : (uint64_t)d2;
   k_kick_drift<<<nb(c.n, 256), 256, 0, c.stream>>>(c.pos, c.vel, c.frc, c.n, hdtm, dtu, kick_only ? 0 : 1,
                                                    track ? c.x_build : nullptr, d2max, c.status, skin_flag,
-                                                   zero_acc);
+                                                   zero_acc, pre ? 1 : 0, hpre);
   return cudaGetLastError();
 }
 

@@ -315,6 +315,10 @@ struct Ctx {
   double* frc = nullptr;   // [3][n] forces of the last evaluation
   double* frc_alt = nullptr;
   bool forces_valid = false;
+  // closing half kick of the last integrated step, not yet applied: velocities
+  // are at the half step and v += kick_hdtm * F is due (see lj_integrate_step)
+  bool kick_pending = false;
+  double kick_hdtm = 0.0;
 
   // binning
   int binned_nc = 0;       // n_c of the current cell order (0 = not binned)
@@ -438,7 +442,8 @@ cudaError_t force_lc_f64(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t force_vl_f32(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t force_vl_f64(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track,
-                              uint32_t* skin_flag = nullptr, double* zero_acc = nullptr);
+                              uint32_t* skin_flag = nullptr, double* zero_acc = nullptr, bool pre = false,
+                              double hpre = 0.0);
 cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s);
 cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s);
 cudaError_t launch_feature_stats(Ctx& c, unsigned long long* stats);

@@ -203,6 +203,39 @@ def test_integrator_matches_oracle_fp64(lj, cfg_args):
     d.close()
 
 
+@pytest.mark.parametrize("cfg_args", [(1, 3, 4, 0), (0, 3, 2, 0)])
+def test_pending_kick_is_exact(lj, cfg_args):
+    """The closing half kick of a call is left pending and fused into the next
+    call's first kick (or applied by a reader): one call of 20 steps, 20 calls
+    of one step, and two calls of 10 with a kinetic-energy read in between give
+    bit-identical states (deterministic N3-off kernels), which match the FP64
+    oracle's velocity Verlet on the FP64 path."""
+    s = W.stratified(4000, 0.7, 31, T=1.0)
+    cfg = lj.config(*cfg_args)
+    out = []
+    for mode in ("one_call", "many_calls", "read_between"):
+        d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
+        d.set_particles(s.pos, s.vel)
+        if mode == "one_call":
+            d.integrate(0.002, 20, cfg)
+        elif mode == "many_calls":
+            for _ in range(20):
+                d.integrate(0.002, 1, cfg)
+        else:
+            d.integrate(0.002, 10, cfg)
+            ke = d.kinetic_energy()
+            assert ke > 0
+            d.integrate(0.002, 10, cfg)
+        out.append(d.state())
+        d.close()
+    for p, v in out[1:]:
+        assert np.array_equal(p, out[0][0]) and np.array_equal(v, out[0][1])
+    p_ref, v_ref, _, _, _ = oracle.vv_run(s.pos, s.vel, s.L, s.rc, 1.0, 0.002, 20, use_cells=True)
+    dp = np.abs(out[0][0].astype(np.int64) - p_ref.astype(np.int64))
+    assert np.minimum(dp, 2 ** 32 - dp).max() <= 2
+    assert np.abs(out[0][1] - v_ref).max() <= 1e-9 * np.abs(v_ref).max()
+
+
 @pytest.mark.parametrize("cfg_args", [(1, 5, 0, 0), (1, 3, 8, 1), (0, 0, 0, 1), (1, 5, 0, 2)])
 def test_md_run_fp32_vs_fp64_library(lj, cfg_args):
     """100 steps with Verlet rebuilds every 10 (and the skin check) on FP32 and
