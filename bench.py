@@ -51,7 +51,7 @@ WORKLOAD = ("homogeneous LJ fluid, 1,048,576 particles, density 0.75 (L=111.82),
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--particles", type=int, default=1048576)
@@ -81,7 +81,7 @@ def dist_setup(args):
 
 
 class ClockSampler:
-    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi SM clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -96,7 +96,7 @@ class ClockSampler:
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -140,25 +140,28 @@ def reduce_over_ranks(pg, seconds, pairs, device=None):
     return float(tmax[0]), float(tsum[1])
 
 
-def traffic_from_profiles(cfg_name):
-    """DRAM bytes per force-kernel launch from the committed ncu summary, if it
-    was taken for this configuration (line: 'traffic <config> <bytes>')."""
+def from_profiles(key, cfg_name):
+    """A figure of the committed ncu summary of the force kernel, if it was
+    taken for this configuration (lines: '<key> <config> <value>'; keys:
+    traffic = DRAM bytes per launch, l1_lsu_pct / issue_pct = L1 data-pipe
+    wavefronts and issue slots, % of peak)."""
     path = os.path.join(ROOT, "profiles", "force_c2_traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         parts = line.split()
-        if len(parts) == 3 and parts[0] == "traffic" and parts[1] == cfg_name:
+        if len(parts) == 3 and parts[0] == key and parts[1] == cfg_name:
             return float(parts[2])
     return None
 
 
-def cpu_oracle_rate(system, evals_max=3, budget_s=25.0):
-    """The FP64 oracle's linked-cell force evaluation on the host cores."""
+def cpu_oracle_rate(system, evals_max=500, budget_s=25.0, min_s=10.0):
+    """The FP64 oracle's linked-cell force evaluation on the host cores,
+    repeated until about min_s seconds of work (at most evals_max, budget_s)."""
     import oracle
     oracle.build()
     t_total, pairs_total, k = 0.0, 0, 0
-    while k < evals_max and t_total < budget_s:
+    while k < evals_max and t_total < min(min_s, budget_s):
         t0 = time.perf_counter()
         _, _, _, npairs = oracle.forces_cells(system.pos, system.L, system.rc)
         t_total += time.perf_counter() - t0
@@ -176,11 +179,15 @@ def run_reference(args, ws, rank, pg):
         cpu_oracle_rate(s, evals_max=1)
     times, pairs = [], []
     import oracle
+    # each step is one full evaluation; the run stops after about a minute of
+    # oracle work (the rate is what is reported)
     for _ in range(args.steps):
         t0 = time.perf_counter()
         _, _, _, npairs = oracle.forces_cells(s.pos, s.L, s.rc)
         times.append(time.perf_counter() - t0)
         pairs.append(npairs)
+        if sum(times) > 60.0:
+            break
     value = float(np.sum(pairs) / np.sum(times))
     line = {
         "impl": "reference", "metric": "LJ in-cutoff pair evals/s", "value": value, "unit": "pairs/s",
@@ -189,7 +196,8 @@ def run_reference(args, ws, rank, pg):
         "config": {"workload": WORKLOAD + "; reference step = one FP64 linked-cell force evaluation (no time step)",
                    "n": s.n},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"{args.steps} full linked-cell force evaluations of the {s.n}-particle system"},
+                         "sample": f"{len(times)} full linked-cell force evaluations of the {s.n}-particle system "
+                                   f"({sum(times):.1f} s)"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -275,7 +283,7 @@ def run_ours(args, ws, rank, local, pg):
     flops_launch = FLOPS_PER_PAIR[cfg.newton3] * float(np.mean(pairs))
     achieved = flops_launch / avg_force_s / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = traffic_from_profiles(cfg_name)
+    traffic = from_profiles("traffic", cfg_name)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel_ms": avg_force_s * 1e3,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FFMA)",
@@ -289,6 +297,12 @@ def run_ours(args, ws, rank, local, pg):
         roof["hbm_gbs"] = traffic / avg_force_s / 1e9
         roof["hbm_frac"] = roof["hbm_gbs"] / hbm_peak
         roof["hbm_peak_gbs"] = hbm_peak
+    l1, issue = from_profiles("l1_lsu_pct", cfg_name), from_profiles("issue_pct", cfg_name)
+    if l1 is not None:
+        # the unit that binds this kernel (ncu): L1 data-pipe wavefronts of the
+        # position gathers and list loads, ahead of issue slots and DRAM
+        roof["limiter"] = {"unit": "L1 data pipe (LSU wavefronts)", "pct_of_peak": l1, "issue_active_pct": issue,
+                           "source": "ncu --set full, profiles/force_vl_jsplit4_c2.md"}
 
     # end to end through the public API with host buffers: positions (doubles)
     # from pinned host memory in, one force evaluation, forces back to host
