@@ -169,6 +169,33 @@ lj_status lj_integrate_step(lj_ctx* ctx, double dt, int32_t nsteps, int32_t rebu
  * not timed).  Errors: LJ_ERR_STATE, LJ_ERR_ARG, LJ_ERR_CUDA. */
 lj_status lj_tune(lj_ctx* ctx, int32_t kind, int32_t samples, lj_config* chosen, double* times_ms);
 
+/* Energy as the tuning metric (Sec. 2.3.3; Sec. 5.2 reports that the energy-
+ * and runtime-optimal orders can differ).  The source is the GPU's total-energy
+ * counter, read through NVML (loaded at run time; read-only calls).
+ *
+ * lj_energy_read: *mj = the counter of CUDA device `device` (-1 = current) in
+ * millijoules since the driver loaded.
+ *
+ * lj_energy_period: polls the counter for probe_ms and returns in *period_ms
+ * the median interval between its updates (NaN if fewer than 3 updates).
+ *
+ * lj_tune_energy: full search by energy.  Every valid configuration runs a
+ * warm-up evaluation, then a batch of force evaluations lasting at least
+ * min_ms (Verlet lists rebuilt every rebuild period, linked cells rebinned per
+ * evaluation, as in lj_tune's cost).  The energy per evaluation is the average
+ * power between two counter updates inside the batch (a host thread records
+ * them) times the time per evaluation.  time_ms and energy_mj (host, may be
+ * NULL, lj_config_list order, NaN when not measured) receive both, and *chosen
+ * the configuration of least energy.  min_ms should span at least 3 counter
+ * periods; with fewer, energies are NaN and LJ_ERR_STATE is returned if none
+ * was measured.
+ *
+ * Errors: LJ_ERR_STATE when NVML or the counter is not available, LJ_ERR_CUDA,
+ * LJ_ERR_ARG; lj_tune_energy also those of lj_compute_forces. */
+lj_status lj_energy_read(int32_t device, double* mj);
+lj_status lj_energy_period(int32_t device, double probe_ms, double* period_ms);
+lj_status lj_tune_energy(lj_ctx* ctx, double min_ms, lj_config* chosen, double* time_ms, double* energy_mj);
+
 /* Full-search selection rule alone (host, no GPU): given `samples` timings per
  * configuration (row-major [n_cfg][samples], NaN = missing) and a validity
  * mask, reduce each row (reduce 0 = mean, 1 = minimum) and return the index

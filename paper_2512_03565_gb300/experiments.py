@@ -15,7 +15,10 @@
 * ``ensemble``: the 256-box batch in one persistent launch vs the same boxes
   run one after another.
 
-Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble [options]
+* ``energy``: time and energy per evaluation of every configuration on four
+  systems, and whether the runtime-best and energy-best choices differ.
+
+Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|energy [options]
 """
 from __future__ import annotations
 
@@ -187,9 +190,37 @@ def ensemble(nboxes=256, steps=1000, dt=0.002, seq_boxes=None, log=print):
     return out
 
 
+def energy(min_ms=1000.0, log=print):
+    """Energy vs runtime as the tuning metric (Sec. 2.3.3, Sec. 5.2): every
+    configuration's time and energy per evaluation (GPU energy counter) on a
+    homogeneous fluid, a dilute gas, a dense FCC solid and a liquid/vapour
+    slab; reports whether the runtime-best and energy-best choices differ."""
+    period = lj.energy_period(probe_ms=1000.0)
+    window = max(min_ms, 8.0 * period) if np.isfinite(period) else min_ms
+    systems = [W.config2(), W.homogeneous(500_000, 0.1, W.BASE_SEED + 71), W.fcc(1_000_000, 1.0, W.BASE_SEED + 72),
+               W.slab(400_000, 0.8, 0.02, 0.5, W.BASE_SEED + 73)]
+    out = {"counter_period_ms": period, "window_ms": window, "systems": []}
+    for s in systems:
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos, s.vel)
+        cfg, ev = d.tune_energy(min_ms=window)
+        d.close()
+        ran = {k: v for k, v in ev.items() if not np.isnan(v[1])}
+        t_best = min(ran, key=lambda k: ran[k][0])
+        e_best = min(ran, key=lambda k: ran[k][1])
+        r = {"system": s.name, "n": s.n, "runtime_best": t_best, "energy_best": e_best,
+             "energy_of_runtime_best_over_best": ran[t_best][1] / ran[e_best][1],
+             "time_of_energy_best_over_best": ran[e_best][0] / ran[t_best][0],
+             "watts_runtime_best": ran[t_best][1] / ran[t_best][0], "configs": ran}
+        out["systems"].append(r)
+        log(f"{s.name}: runtime-best {t_best} ({ran[t_best][0]:.4f} ms, {ran[t_best][1]:.1f} mJ), "
+            f"energy-best {e_best} ({ran[e_best][0]:.4f} ms, {ran[e_best][1]:.1f} mJ)")
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble"])
+    ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "energy"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--data", default="gpurun_out/tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
@@ -222,6 +253,11 @@ def main(argv=None):
                 json.dump(summ, open(a.out, "w"))
     elif a.what == "ensemble":
         res = ensemble(steps=a.steps)
+        if a.out:
+            json.dump(res, open(a.out, "w"))
+    elif a.what == "energy":
+        res = energy()
+        print(json.dumps({k: v for k, v in res.items() if k != "systems"}))
         if a.out:
             json.dump(res, open(a.out, "w"))
     else:

@@ -76,6 +76,9 @@ _SIGS = {
     "lj_config_list": (C.c_int32, [_VP, C.c_int32]),
     "lj_integrate_step": (C.c_int, [_VP, C.c_double, C.c_int32, C.c_int32, lj_config]),
     "lj_tune": (C.c_int, [_VP, C.c_int32, C.c_int32, C.POINTER(lj_config), _VP]),
+    "lj_energy_read": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
+    "lj_energy_period": (C.c_int, [C.c_int32, C.c_double, C.POINTER(C.c_double)]),
+    "lj_tune_energy": (C.c_int, [_VP, C.c_double, C.POINTER(lj_config), _VP, _VP]),
     "lj_tune_select": (C.c_int32, [_VP, C.c_int32, C.c_int32, _VP, C.c_int32]),
     "lj_features": (C.c_int, [_VP, _VP]),
     "lj_tuner_set_model": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, _VP]),
@@ -110,6 +113,24 @@ _SIGS = {
 def exported_symbols():
     """Names of the entry points this binding expects the library to export."""
     return list(_SIGS)
+
+
+def energy_read(device=-1):
+    """The GPU's total-energy counter in millijoules (NVML), or raises LJError."""
+    v = C.c_double()
+    st = load().lj_energy_read(int(device), C.byref(v))
+    if st != LJ_OK:
+        raise LJError(st, "GPU energy counter unavailable")
+    return v.value
+
+
+def energy_period(device=-1, probe_ms=500.0):
+    """Median update interval (ms) of the GPU's total-energy counter."""
+    v = C.c_double()
+    st = load().lj_energy_period(int(device), float(probe_ms), C.byref(v))
+    if st != LJ_OK:
+        raise LJError(st, "GPU energy counter unavailable")
+    return v.value
 
 
 def load():
@@ -297,6 +318,16 @@ class Domain:
         chosen = lj_config()
         self._check(self.lib.lj_tune(self.h, kind, samples, C.byref(chosen), times.ctypes.data))
         return chosen, dict(zip((config_name(c) for c in all_cfg), times))
+
+    def tune_energy(self, min_ms=1000.0):
+        """Full search by energy per evaluation (GPU energy counter); returns the
+        chosen configuration and {name: (ms, mJ) per evaluation}."""
+        all_cfg = configs()
+        t = np.full(len(all_cfg), np.nan)
+        e = np.full(len(all_cfg), np.nan)
+        chosen = lj_config()
+        self._check(self.lib.lj_tune_energy(self.h, float(min_ms), C.byref(chosen), t.ctypes.data, e.ctypes.data))
+        return chosen, {config_name(c): (float(a), float(b)) for c, a, b in zip(all_cfg, t, e)}
 
     def set_tuner_model(self, params, C_out, mean, std, cfgs):
         p = np.ascontiguousarray(params, dtype=np.float32)

@@ -99,3 +99,14 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     with pytest.raises(RuntimeError, match="not built"):
         mod.load()
     importlib.reload(ljgb)
+
+
+def test_energy_counter_absent_is_a_status_not_a_crash():
+    """Without a GPU (or NVML) the energy path returns a status code."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: covered by the GPU tests")
+    from paper_2512_03565_gb300 import ljgb as lj
+    with pytest.raises(lj.LJError) as e:
+        lj.energy_read()
+    assert e.value.status in (lj.LJ_ERR_STATE, lj.LJ_ERR_CUDA)

@@ -70,3 +70,26 @@ def test_learned_tuner_gain_on_held_out_systems(lj, system):
     assert t_l <= 1.15 * best, (lj.config_name(learned), t_l, best)
     assert t_l <= t_default * 1.02
     assert t_learned < 0.1 * t_full
+
+
+def test_energy_counter_and_energy_tuner(lj):
+    """Sec. 2.3.3: energy per evaluation as the tuning metric.  The GPU's
+    energy counter only increases; the energy tuner returns the configuration
+    of least measured energy per evaluation, with finite times and energies
+    for every configuration it ran."""
+    e0 = lj.energy_read()
+    period = lj.energy_period(probe_ms=300.0)
+    e1 = lj.energy_read()
+    assert e1 >= e0 > 0
+    assert np.isfinite(period) and 0 < period < 1000
+    s = W.stratified(60000, 0.6, 43)
+    d = lj.Domain(s.L, s.rc, s.skin)
+    d.set_particles(s.pos, s.vel)
+    cfg, ev = d.tune_energy(min_ms=4 * period)
+    d.close()
+    ran = {k: v for k, v in ev.items() if not np.isnan(v[1])}
+    assert len(ran) == 33
+    # power = energy / time per evaluation: a busy GB300 draws between its
+    # idle floor and its 1.4 kW limit
+    assert all(v[0] > 0 and 100.0 < v[1] / v[0] < 1500.0 for v in ran.values())
+    assert lj.config_name(cfg) == min(ran, key=lambda k: ran[k][1])
