@@ -304,27 +304,48 @@ def run_ours(args, ws, rank, local, pg):
         roof["limiter"] = {"unit": "L1 data pipe (LSU wavefronts)", "pct_of_peak": l1, "issue_active_pct": issue,
                            "source": "ncu --set full, profiles/force_vl_jsplit4_c2.md"}
 
-    # end to end through the public API with host buffers: positions (doubles)
-    # from pinned host memory in, one force evaluation, forces back to host
+    # end to end through the public API with host buffers, as a host-driven
+    # time loop makes the calls: each step uploads that step's positions
+    # (doubles, caller's order, pinned host memory) with lj_update_positions,
+    # evaluates the forces (the lists are kept while the skin allows and
+    # rebuilt when it does not) and reads the forces back to pinned host
+    # memory.  The positions are those of a 30-step MD trajectory of the same
+    # system, computed beforehand outside the timed region.
     e2e = None
     if not args.no_e2e:
-        x_host = torch.from_numpy((s.pos.astype(np.float64) + 0.5) * (s.L / 2.0 ** 32)).pin_memory()
+        k_e2e = 30
+        d_t = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP32_ACC64, stream=stream)
+        d_t.set_particles(s.pos, s.vel)
+        traj = []
+        for _ in range(k_e2e + 2):
+            d_t.integrate(dt, 1, cfg, rebuild_every=rebuild)
+            p_fp, _ = d_t.state()
+            traj.append(torch.from_numpy((p_fp.astype(np.float64) + 0.5) * (s.L / 2.0 ** 32)).pin_memory())
+        d_t.close()
         f_host = torch.empty((3, s.n), dtype=torch.float64).pin_memory()
         lib = lj.load()
-        k_e2e = max(3, min(args.steps, 10))
+        d.set_particles(s.pos, s.vel)
+        st = lib.lj_compute_forces(d.h, cfg, None, None)
+        builds0 = 0
         for it in range(k_e2e + 2):
             if it == 2:
                 torch.cuda.synchronize(dev)
+                builds0 = int(d.counters()[2])
                 t0 = time.perf_counter()
-            st = lib.lj_set_particles(d.h, s.n, x_host.data_ptr(), None, 1.0, 0)
+                np_sum = 0
+            st = st or lib.lj_update_positions(d.h, traj[it].data_ptr(), 0)
             st = st or lib.lj_compute_forces(d.h, cfg, None, None)
             st = st or lib.lj_get_forces(d.h, f_host.data_ptr(), 0)
             if st:
                 raise lj.LJError(st, lib.lj_last_error(d.h).decode())
+            if it >= 2:
+                np_sum += int(d.counters()[1])
         t_e2e = (time.perf_counter() - t0) / k_e2e
-        np_e2e = int(d.counters()[1])
-        e2e = {"value": np_e2e / t_e2e * ws, "unit": "pairs/s", "h2d_bytes_per_step": 3 * s.n * 8,
-               "d2h_bytes_per_step": 3 * s.n * 8, "ms_per_step": t_e2e * 1e3}
+        builds = int(d.counters()[2]) - builds0
+        e2e = {"value": np_sum / k_e2e / t_e2e * ws, "unit": "pairs/s", "h2d_bytes_per_step": 3 * s.n * 8,
+               "d2h_bytes_per_step": 3 * s.n * 8, "ms_per_step": t_e2e * 1e3, "steps": k_e2e,
+               "list_builds": builds,
+               "path": "lj_update_positions + lj_compute_forces + lj_get_forces per step, MD trajectory inputs"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -120,6 +120,17 @@ lj_status lj_set_particles(lj_ctx* ctx, int64_t n, const double* pos, const doub
 lj_status lj_set_particles_fp(lj_ctx* ctx, int64_t n, const uint32_t* pos_fp, const double* vel,
                               double mass, int on_device);
 
+/* New positions for the loaded particles (caller's order, n as loaded,
+ * float64 [3][n], host or device), velocities kept.  Unlike lj_set_particles
+ * the cell order and the Verlet lists are kept: the next force evaluation
+ * reuses the lists while every particle stays within skin/2 of its position
+ * at the last build and rebuilds them otherwise (Sec. 2.1.1: lists are kept
+ * over several steps thanks to the skin); linked cells are rebinned.  This
+ * is the call of a host-driven time loop.  A pending closing kick (see
+ * lj_integrate_step) is applied first.  Errors: LJ_ERR_ARG, LJ_ERR_STATE (no
+ * particles loaded), LJ_ERR_CUDA. */
+lj_status lj_update_positions(lj_ctx* ctx, const double* pos, int32_t on_device);
+
 /* Bin the particles into the cells of one container by a stable counting sort
  * on the cell id (Sec. 2.1.1, Linked Cells): cells of edge >= r_c (LJ_LC) or
  * >= r_c + skin (LJ_VL), n_c = floor(L / edge) per axis, at least 3.  The

@@ -530,6 +530,34 @@ lj_status lj_set_particles_fp(lj_ctx* h, int64_t n, const uint32_t* pos_fp, cons
   return set_particles_impl(h, n, pos_fp, true, vel, mass, on_device);
 }
 
+lj_status lj_update_positions(lj_ctx* h, const double* pos, int32_t on_device) {
+  if (!h || !pos) return LJ_ERR_ARG;
+  Ctx& c = h->c;
+  CKS(need_particles(c));
+  CKS(settle_kick(c));  // the pending kick belongs to the state being replaced
+  const size_t pbytes = 3 * (size_t)c.n * sizeof(double);
+  const double* dpos = pos;
+  if (!on_device) {
+    if (c.stage_bytes < pbytes) {
+      dfree(c.stage);
+      c.stage = nullptr;
+      c.stage_bytes = 0;
+      CK(cudaMalloc(&c.stage, pbytes));
+      c.stage_bytes = pbytes;
+    }
+    CK(cudaMemcpyAsync(c.stage, pos, pbytes, cudaMemcpyHostToDevice, c.stream));
+    dpos = (const double*)c.stage;
+  }
+  CK(launch_update_pos(c.pos, dpos, c.n, c.L, c.stream));
+  c.launches += 1;
+  // the cell order and the lists stay; the next evaluation rebins (linked
+  // cells) or checks the skin and rebuilds only when needed (Verlet lists)
+  c.moved = true;
+  c.moved_since_build = true;
+  c.forces_valid = false;
+  return LJ_OK;
+}
+
 lj_status lj_bin_cells(lj_ctx* h, int32_t container) {
   if (!h) return LJ_ERR_ARG;
   Ctx& c = h->c;

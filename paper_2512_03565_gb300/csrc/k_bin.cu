@@ -18,6 +18,14 @@ namespace ljgb {
 
 // x_fp = floor(x / L * 2^32) mod 2^32 (the division and floors are exact
 // IEEE-754 operations, so the host oracle's identical formula agrees bit for bit).
+__device__ __forceinline__ uint32_t quantize_coord(double x, double L) {
+  double t = x / L;
+  t = t - floor(t);
+  double s = floor(t * 4294967296.0);
+  if (s >= 4294967296.0) s = 0.0;
+  return (uint32_t)s;
+}
+
 __global__ void k_quantize(const double* __restrict__ pos, int64_t n, double L, const double* __restrict__ vel,
                            uint4* __restrict__ out, double* __restrict__ vout) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -25,14 +33,19 @@ __global__ void k_quantize(const double* __restrict__ pos, int64_t n, double L, 
   uint32_t q[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double t = pos[a * n + i] / L;
-    t = t - floor(t);
-    double s = floor(t * 4294967296.0);
-    if (s >= 4294967296.0) s = 0.0;
-    q[a] = (uint32_t)s;
+    q[a] = quantize_coord(pos[a * n + i], L);
     vout[a * n + i] = vel ? vel[a * n + i] : 0.0;
   }
   out[i] = make_uint4(q[0], q[1], q[2], (uint32_t)i);
+}
+
+// New coordinates in the caller's order written into the current (cell)
+// order: slot s takes those of its particle pos[s].w, quantised as above.
+__global__ void k_update_pos(uint4* __restrict__ pos, const double* __restrict__ x, int64_t n, double L) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t o = pos[s].w;
+  pos[s] = make_uint4(quantize_coord(x[o], L), quantize_coord(x[n + o], L), quantize_coord(x[2 * n + o], L), o);
 }
 
 __global__ void k_load_fp(const uint32_t* __restrict__ pos, int64_t n, const double* __restrict__ vel,
@@ -49,6 +62,11 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 cudaError_t launch_quantize(const double* pos, int64_t n, double L, const double* vel, uint4* out_pos,
                             double* out_vel, cudaStream_t s) {
   k_quantize<<<nblk(n, 256), 256, 0, s>>>(pos, n, L, vel, out_pos, out_vel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_pos(uint4* pos, const double* x, int64_t n, double L, cudaStream_t s) {
+  k_update_pos<<<nblk(n, 256), 256, 0, s>>>(pos, x, n, L);
   return cudaGetLastError();
 }
 

@@ -423,6 +423,7 @@ cudaError_t excl_scan_u32(Ctx& c, const uint32_t* in, uint32_t* out, int64_t n);
 cudaError_t sort_segments(Ctx& c, const uint32_t* starts, int64_t nseg, unsigned long long* key,
                           unsigned long long* key2);
 cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen);
+cudaError_t launch_update_pos(uint4* pos, const double* x, int64_t n, double L, cudaStream_t s);
 cudaError_t launch_reverse_index(Ctx& c);
 cudaError_t launch_list_to16(Ctx& c, uint32_t* overflow);
 

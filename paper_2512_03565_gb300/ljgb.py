@@ -69,6 +69,7 @@ _SIGS = {
                                  C.c_double, C.c_int, _VP]),
     "lj_set_particles": (C.c_int, [_VP, C.c_int64, _VP, _VP, C.c_double, C.c_int]),
     "lj_set_particles_fp": (C.c_int, [_VP, C.c_int64, _VP, _VP, C.c_double, C.c_int]),
+    "lj_update_positions": (C.c_int, [_VP, _VP, C.c_int32]),
     "lj_bin_cells": (C.c_int, [_VP, C.c_int32]),
     "lj_build_verlet": (C.c_int, [_VP, C.c_int32]),
     "lj_compute_forces": (C.c_int, [_VP, lj_config, _VP, _VP]),
@@ -232,6 +233,12 @@ class Domain:
         self._check(fn(self.h, n, pp, vp, mass, pdev))
         self.n = n
         self.mass = mass
+
+    def update_positions(self, pos):
+        """New (3, n) float64 coordinates of the loaded particles (caller's
+        order); cell order and Verlet lists are kept while the skin allows."""
+        pp, pdev, keep = _ptr(pos, np.float64)
+        self._check(self.lib.lj_update_positions(self.h, pp, pdev))
 
     def bin_cells(self, container):
         self._check(self.lib.lj_bin_cells(self.h, container))

@@ -172,6 +172,41 @@ def test_verlet_lists_bit_exact_edge(lj, name, L, pos):
     d.close()
 
 
+def test_update_positions_keeps_lists_while_the_skin_allows(lj):
+    """lj_update_positions keeps the cell order and lists: small moves reuse
+    the lists (no build), a move beyond skin/2 triggers one, and the forces
+    equal those of a fresh context loaded with the same coordinates (FP64) and
+    the oracle's."""
+    s = W.stratified(5000, 0.7, 51)
+    cfg = lj.config(lj.LJ_VL, lj.LJ_ORD_JSPLIT, 4)
+    x0 = (s.pos.astype(np.float64) + 0.5) * (s.L / 2.0 ** 32)
+    d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
+    d.set_particles(x0, s.vel)
+    d.compute_forces(cfg)
+    builds = d.counters()[2]
+    rng = np.random.default_rng(7)
+    small = x0 + rng.uniform(-0.05, 0.05, size=x0.shape)     # |move| < skin/2 = 0.15
+    large = small.copy()
+    large[:, 17] += 0.4                                        # one particle beyond skin/2
+    for x, rebuilt in ((small, False), (large, True)):
+        d.update_positions(x)
+        d.compute_forces(cfg)
+        assert (d.counters()[2] > builds) == rebuilt
+        builds = d.counters()[2]
+        ref = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP64)
+        ref.set_particles(x, s.vel)
+        ref.compute_forces(cfg)
+        F_ref = ref.forces()
+        ref.close()
+        assert rel_err(d.forces(), F_ref) <= 1e-12
+        q = np.array([[oracle.quantize(v, s.L) for v in row] for row in x], dtype=np.uint32)
+        F_orc, _, _, _ = oracle.forces_bruteforce(q, s.L, s.rc)
+        assert rel_err(d.forces(), F_orc) <= 1e-12
+    pos, vel = d.state()
+    assert np.array_equal(vel, s.vel)                           # velocities untouched
+    d.close()
+
+
 def test_quantization_matches_oracle(lj):
     rng = np.random.default_rng(5)
     L = 12.345
