@@ -311,9 +311,20 @@ typedef struct lj_ens lj_ens;
 lj_status lj_ensemble_create(lj_ens** out, int32_t nboxes, const double* box_L, const int64_t* counts,
                              const uint32_t* pos_fp, const double* vel, double cutoff, double eps, double sigma,
                              double mass, void* cuda_stream);
+/* Verlet-list mode (Sec. 2.1.1) for the whole batch: with skin > 0 every box
+ * bins on cells of edge >= cutoff + skin and keeps Verlet lists (the builder
+ * of lj_build_verlet, one warp per cell, whole-box lists for boxes of fewer
+ * than 3 such cells per axis), rebuilt inside the launch every rebuild_every
+ * steps or when a particle moved beyond skin/2 since the last build; forces
+ * use the JSPLIT<w> list order.  skin = 0 returns to linked cells rebinned
+ * every step.  cap = list capacity per particle (0 = from the densest box).
+ * A list longer than cap stops the run mid-step with LJ_ERR_CAPACITY.
+ * Errors: LJ_ERR_ARG, LJ_ERR_OOM, LJ_ERR_CUDA. */
+lj_status lj_ensemble_set_lists(lj_ens* ens, double skin, int32_t rebuild_every, int32_t cap);
 /* nsteps steps of every box in one launch (initial forces first if none are
  * current); use_graph = 1 captures the launch as a CUDA graph and replays it.
- * Synchronises.  Errors: LJ_ERR_ARG, LJ_ERR_TIMEOUT, LJ_ERR_NONFINITE, LJ_ERR_CUDA. */
+ * Synchronises.  Errors: LJ_ERR_ARG, LJ_ERR_TIMEOUT, LJ_ERR_NONFINITE,
+ * LJ_ERR_CAPACITY (list mode), LJ_ERR_CUDA. */
 lj_status lj_ensemble_run(lj_ens* ens, double dt, int32_t nsteps, int32_t use_graph);
 /* Autotunes the launch shape (JSPLIT width w in {2,4,8,16}, block size in
  * {128,256,512}) by timing `steps` steps of each on a copy of the state. */

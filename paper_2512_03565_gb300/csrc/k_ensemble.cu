@@ -20,6 +20,7 @@
 #include <cmath>
 #include <vector>
 
+#include "k_build.cuh"
 #include "k_force_lc.cuh"
 
 namespace ljgb {
@@ -35,6 +36,12 @@ struct EnsBox {
   int32_t n;
   int64_t off;      // first particle
   int64_t cell_off; // first cell
+  // Verlet-list mode (lj_ensemble_set_lists): cells of edge >= r_c + skin
+  int32_t ncv;      // cells per axis (1 = the whole box is one cell)
+  int64_t cell_off_v;
+  uint64_t Rl2;     // floor(((r_c + skin)/u)^2)
+  float rl2p_lo, rl2p_hi;
+  uint64_t skin2;   // (skin / 2 / u)^2: displacement that forces a rebuild
 };
 
 struct EnsArgs {
@@ -64,6 +71,17 @@ struct EnsArgs {
   int first_force;       // compute forces at the initial positions first
   uint32_t spin_limit;   // barrier wait bound (iterations of ~0.1 us)
   int skip_block;        // test hook: this block leaves before the first barrier (-1 = none)
+  // Verlet-list mode
+  int vl;                // 0: linked cells rebinned every step; 1: Verlet lists
+  int rebuild_every;
+  int cap;               // list capacity (row-major rows of cap entries)
+  int64_t ncells_v;
+  const uint16_t* cell_box_v;  // box of each list-grid cell
+  int32_t* nbr;
+  int32_t* nnbr;
+  uint32_t* xb;          // [3][ntot] positions at the last build
+  uint32_t* since_build; // steps since the last build (device word)
+  uint32_t* skin_flag;   // a particle moved beyond skin/2 (device word)
 };
 
 constexpr int ENS_SCAN_I = 8;  // items per thread of the in-kernel scan
@@ -227,6 +245,111 @@ __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __rest
   }
 }
 
+// Forces over the Verlet lists (JSPLIT<W>: W lanes per particle stride over
+// its row), the pair arithmetic of the single-box list kernels with the box's
+// parameters.
+template <int W>
+__device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __restrict__ pos,
+                                              double* __restrict__ fx) {
+  constexpr int G = 32 / W;
+  const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n = A.ntot;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * G < n; w += nwarps) {
+    const int64_t i = w * G + g;
+    const bool vi = i < n;
+    const EnsBox B = A.boxes[vi ? (int)A.box_of[i] : 0];
+    const LJParams P = box_params(B);
+    float ax = 0.f, ay = 0.f, az = 0.f, eu = 0.f, ew = 0.f;
+    int cnt = 0;
+    if (vi) {
+      const uint4 pi = pos[i];
+      const int m = min(A.nnbr[i], A.cap);
+      const int32_t* row = A.nbr + i * A.cap;
+      for (int k0 = sub; k0 < m; k0 += W * 4) {
+        int jc[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) jc[t] = (k0 + t * W < m) ? __ldcs(row + k0 + t * W) : (int)i;
+        uint4 pj[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) pj[t] = __ldg(pos + jc[t]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          float af, bf, cf;
+          const float fac = pair_f32<false, false, true>(mimg(pi.x, pj[t].x), mimg(pi.y, pj[t].y),
+                                                         mimg(pi.z, pj[t].z), P, af, bf, cf, eu, ew, cnt);
+          ax += fac * af;
+          ay += fac * bf;
+          az += fac * cf;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+      az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    unsigned long long wc = (unsigned long long)cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
+    if (lane == 0 && wc) atomicAdd(A.npairs, wc);
+    if (vi && sub == 0) {
+      const double f0 = -B.e24u * f2d_exact(ax), f1 = -B.e24u * f2d_exact(ay), f2 = -B.e24u * f2d_exact(az);
+      fx[i] = f0;
+      fx[n + i] = f1;
+      fx[2 * n + i] = f2;
+      if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2)) atomicOr(A.status, ST_NONFINITE);
+    }
+  }
+}
+
+// The list build of every box: one warp per cell of the list grid, the cell's
+// particles in tiles of <= 32 (bv_tile), against the 27 cells around it (the
+// whole box when it holds fewer than 3 cells per axis).  Records the build
+// positions for the skin check.
+__device__ __forceinline__ void ens_build_lists(const EnsArgs& A, const uint4* __restrict__ pos,
+                                                const uint32_t* __restrict__ cs) {
+  __shared__ uint4 s_i[16][32];  // blocks of at most 512 threads
+  __shared__ float4 s_c[16][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n = A.ntot;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < A.ncells_v; c += nwarps) {
+    const uint32_t cb = cs[c], ce = cs[c + 1];
+    if (cb == ce) continue;
+    const EnsBox& B = A.boxes[A.cell_box_v[c]];
+    BSeg segs[18];
+    int ns;
+    if (B.ncv >= 3) {
+      const int nc = B.ncv;
+      const int64_t local = c - B.cell_off_v;
+      ns = builder_segments(cs + B.cell_off_v, nc, (int)(local / nc), (int)(local % nc), segs);
+    } else {
+      segs[0] = {(uint32_t)B.off, (uint32_t)(B.off + B.n), 0.0f, 0.0f, 0.0f, 1};
+      ns = 1;
+    }
+    for (uint32_t first = cb; first < ce; first += 32) {
+      const int ni = (int)min(32u, ce - first);
+      if (lane < ni) {
+        const uint4 p = pos[first + lane];
+        s_i[wib][lane] = p;
+        s_c[wib][lane] = make_float4(coarse_coord(p.x), coarse_coord(p.y), coarse_coord(p.z), 0.0f);
+        A.xb[first + lane] = p.x;
+        A.xb[n + first + lane] = p.y;
+        A.xb[2 * n + first + lane] = p.z;
+      }
+      const uint32_t cnt = bv_tile<false, false>(pos, segs, ns, first, ni, s_i[wib], s_c[wib], (int)n, A.cap, B.Rl2,
+                                                 B.rl2p_lo, B.rl2p_hi, A.nbr);
+      if (lane < ni) {
+        A.nnbr[first + lane] = (int32_t)cnt;
+        if (cnt > (uint32_t)A.cap) atomicOr(A.status, ST_CAPACITY);
+      }
+      __syncwarp();
+    }
+  }
+}
+
 template <int W>
 __global__ void k_ensemble(EnsArgs A) {
   unsigned gen = 0;
@@ -234,7 +357,6 @@ __global__ void k_ensemble(EnsArgs A) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t scan_tile = (int64_t)blockDim.x * ENS_SCAN_I;
-  const int64_t nscan = (A.ncells + scan_tile - 1) / scan_tile;
   const double M = 6755399441055744.0;  // 1.5 * 2^52: fma(v, dtu, M) rounds v dtu to an integer
   if ((int)blockIdx.x == A.skip_block) return;
   uint4 *pos = A.pos, *pos2 = A.pos_alt;
@@ -242,10 +364,12 @@ __global__ void k_ensemble(EnsArgs A) {
   const int total = A.nsteps + (A.first_force ? 1 : 0);
   for (int step = 0; step < total; ++step) {
     const bool move = !(A.first_force && step == 0);
-    // ---- kick + drift (and, from the second step on, the previous closing kick)
+    // ---- kick + drift (and, from the second step on, the previous closing kick);
+    // with lists, the displacement since the last build is checked (skin/2)
     if (move) {
       for (int64_t i = tid; i < n; i += nthr) {
-        const double dtu = A.boxes[A.box_of[i]].dtu;
+        const EnsBox& B = A.boxes[A.box_of[i]];
+        const double dtu = B.dtu;
         uint4 p = pos[i];
         uint32_t* pc = &p.x;
 #pragma unroll
@@ -255,23 +379,43 @@ __global__ void k_ensemble(EnsArgs A) {
           pc[a] += (uint32_t)__double2loint(__fma_rn(v, dtu, M));
         }
         pos[i] = p;
+        if (A.vl) {
+          const int a = (int)(p.x - A.xb[i]), b = (int)(p.y - A.xb[n + i]), c = (int)(p.z - A.xb[2 * n + i]);
+          const uint64_t d2 = (uint64_t)((long long)a * a) + (uint64_t)((long long)b * b) +
+                              (uint64_t)((long long)c * c);
+          if (d2 > B.skin2) *((volatile uint32_t*)A.skin_flag) = 1u;
+        }
       }
     }
-    // ---- cell ids and counts
-    for (int64_t c = tid; c < A.ncells; c += nthr) A.cnt[c] = 0u;
+    if (A.vl && blockIdx.x == 0 && threadIdx.x == 0) *A.since_build += 1u;
+    // linked cells rebin every step; lists are rebuilt on schedule or when a
+    // particle left its skin (every block reads the same words after the barrier)
+    if (!A.vl)
+      for (int64_t c = tid; c < A.ncells; c += nthr) A.cnt[c] = 0u;
     if (!ens_barrier(A, gen)) return;
+    const bool rebuild = !A.vl || *((volatile uint32_t*)A.since_build) >= (uint32_t)A.rebuild_every ||
+                         *((volatile uint32_t*)A.skin_flag) != 0u;
+    const int64_t ncells = A.vl ? A.ncells_v : A.ncells;
+    if (rebuild) {
+    if (A.vl) {
+      for (int64_t c = tid; c < ncells; c += nthr) A.cnt[c] = 0u;
+      if (!ens_barrier(A, gen)) return;
+    }
+    // ---- cell ids and counts
     for (int64_t i = tid; i < n; i += nthr) {
       const EnsBox& B = A.boxes[A.box_of[i]];
       const uint4 p = pos[i];
-      const uint32_t nc = (uint32_t)B.nc;
-      const uint32_t c = (uint32_t)B.cell_off + (cx_of(p.z, nc) * nc + cx_of(p.y, nc)) * nc + cx_of(p.x, nc);
+      const uint32_t nc = (uint32_t)(A.vl ? B.ncv : B.nc);
+      const uint32_t c = (uint32_t)(A.vl ? B.cell_off_v : B.cell_off) +
+                         (cx_of(p.z, nc) * nc + cx_of(p.y, nc)) * nc + cx_of(p.x, nc);
       A.cell_of[i] = c;
       A.slot[i] = atomicAdd(&A.cnt[c], 1u);
     }
     if (!ens_barrier(A, gen)) return;
     // ---- exclusive scan of the counts over all boxes' cells
+    const int64_t nscan = (ncells + scan_tile - 1) / scan_tile;
     for (int64_t t = blockIdx.x; t < nscan; t += gridDim.x)
-      ens_scan_tile(A.cnt, A.cell_start, A.ncells, t * scan_tile, &A.scan_tot[t]);
+      ens_scan_tile(A.cnt, A.cell_start, ncells, t * scan_tile, &A.scan_tot[t]);
     if (!ens_barrier(A, gen)) return;
     if (blockIdx.x == 0) {
       uint32_t carry = 0;
@@ -285,10 +429,10 @@ __global__ void k_ensemble(EnsArgs A) {
         carry += s_tot;
         __syncthreads();
       }
-      if (threadIdx.x == 0) A.cell_start[A.ncells] = carry;
+      if (threadIdx.x == 0) A.cell_start[ncells] = carry;
     }
     if (!ens_barrier(A, gen)) return;
-    for (int64_t c = tid; c < A.ncells; c += nthr) A.cell_start[c] += A.scan_tot[c / scan_tile];
+    for (int64_t c = tid; c < ncells; c += nthr) A.cell_start[c] += A.scan_tot[c / scan_tile];
     if (!ens_barrier(A, gen)) return;
     // ---- scatter, per-cell sort, permutation
     for (int64_t i = tid; i < n; i += nthr)
@@ -296,7 +440,7 @@ __global__ void k_ensemble(EnsArgs A) {
     if (!ens_barrier(A, gen)) return;
     {
       const int lane = threadIdx.x & 31;
-      for (int64_t c = tid >> 5; c < A.ncells; c += nthr >> 5) {
+      for (int64_t c = tid >> 5; c < ncells; c += nthr >> 5) {
         const uint32_t b = A.cell_start[c], e = A.cell_start[c + 1], m = e - b;
         if (m == 0) continue;
         if (m <= 32) {
@@ -333,8 +477,22 @@ __global__ void k_ensemble(EnsArgs A) {
       double* tf = frc; frc = frc2; frc2 = tf;
     }
     if (!ens_barrier(A, gen)) return;
-    // ---- forces, then the closing kick of this step (fused per particle)
-    ens_forces<W>(A, pos, A.cell_start, frc);
+    if (A.vl) {
+      // ---- list build; a list beyond the capacity stops the run
+      ens_build_lists(A, pos, A.cell_start);
+      if (!ens_barrier(A, gen)) return;
+      if (*((volatile uint32_t*)A.status) & ST_CAPACITY) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *A.since_build = 0u;
+        *A.skin_flag = 0u;
+      }
+    }
+    }  // rebuild
+    // ---- forces, then the closing kick of this step
+    if (A.vl)
+      ens_forces_vl<W>(A, pos, frc);
+    else
+      ens_forces<W>(A, pos, A.cell_start, frc);
     if (!ens_barrier(A, gen)) return;
     if (move) {
       for (int64_t i = tid; i < n; i += nthr)
@@ -361,6 +519,7 @@ struct Ens {
   std::vector<int64_t> counts;
   EnsArgs A{};
   double mass = 1.0, rc = 2.5, eps = 1.0, sigma = 1.0;
+  double skin = 0.0;
   int W = 8, block = 256;
   bool forces_valid = false;
   cudaGraphExec_t gexec = nullptr;
@@ -660,9 +819,24 @@ lj_status lj_ensemble_run(lj_ens* h, double dt, int32_t nsteps, int32_t use_grap
     E.err = "non-finite force";
     return LJ_ERR_NONFINITE;
   }
+  if (st & ST_CAPACITY) {
+    E.err = "a Verlet list outgrew the capacity (lj_ensemble_set_lists with a larger cap); the run stopped mid-step";
+    E.forces_valid = false;
+    return LJ_ERR_CAPACITY;
+  }
   E.forces_valid = true;
   return LJ_OK;
 }
+
+namespace {
+// The next step of a list-mode run rebuilds the lists (after a state that the
+// lists do not describe was put back).
+cudaError_t ens_force_rebuild(Ens& E) {
+  if (!E.A.vl) return cudaSuccess;
+  const uint32_t big = 0x40000000u;
+  return cudaMemcpyAsync(E.A.since_build, &big, sizeof(uint32_t), cudaMemcpyHostToDevice, E.stream);
+}
+}  // namespace
 
 // Chooses the JSPLIT width and block size of the persistent kernel by timing
 // `steps` steps of each candidate on a copy of the state (restored after every
@@ -703,6 +877,7 @@ lj_status lj_ensemble_tune(lj_ens* h, double dt, int32_t steps, int32_t* w_out, 
       cudaMemcpyAsync(A.pos, bp, sizeof(uint4) * n, cudaMemcpyDeviceToDevice, s);
       cudaMemcpyAsync(A.vel, bv, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
       cudaMemcpyAsync(A.frc, bf, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
+      ens_force_rebuild(E);   // every trial starts with a list build (list mode)
       E.forces_valid = true;  // time steps only
       cudaEventRecord(e0, s);
       st = lj_ensemble_run(h, dt, steps, 0);
@@ -722,6 +897,7 @@ lj_status lj_ensemble_tune(lj_ens* h, double dt, int32_t steps, int32_t* w_out, 
   cudaMemcpyAsync(A.pos, bp, sizeof(uint4) * n, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(A.vel, bv, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(A.frc, bf, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
+  ens_force_rebuild(E);
   cudaStreamSynchronize(s);
   E.forces_valid = valid0;
   cudaEventDestroy(e0);
@@ -732,6 +908,101 @@ lj_status lj_ensemble_tune(lj_ens* h, double dt, int32_t steps, int32_t* w_out, 
   if (w_out) *w_out = bw;
   if (block_out) *block_out = bb;
   return st;
+}
+
+lj_status lj_ensemble_set_lists(lj_ens* h, double skin, int32_t rebuild_every, int32_t cap) {
+  if (!h || !(skin >= 0) || rebuild_every < 1 || cap < 0) return LJ_ERR_ARG;
+  Ens& E = h->e;
+  EnsArgs& A = E.A;
+  cudaStream_t s = E.stream;
+  if (skin == 0.0) {  // back to linked cells
+    A.vl = 0;
+    E.skin = 0.0;
+    E.forces_valid = false;
+    return LJ_OK;
+  }
+  const double rl = E.rc + skin;
+  int64_t coff = 0;
+  double rho_max = 0.0;
+  for (auto& B : E.hb) {
+    const int nc = (int)std::floor(B.L / rl);
+    B.ncv = nc >= 3 ? nc : 1;
+    B.cell_off_v = coff;
+    coff += (int64_t)B.ncv * B.ncv * B.ncv;
+    B.Rl2 = ens_cut2(B.L, rl);
+    coarse_band(B.Rl2, &B.rl2p_lo, &B.rl2p_hi);
+    const double hs = 0.5 * skin * 4294967296.0 / B.L;
+    B.skin2 = (uint64_t)std::min(hs * hs, 1.8e19);
+    rho_max = std::max(rho_max, (double)B.n / (B.L * B.L * B.L));
+  }
+  const int64_t ncv = coff, n = E.ntot;
+  if (cap == 0) {  // the densest box's expected list length, with room for fluctuations
+    const double m = 4.18879020478639 * rl * rl * rl * rho_max;
+    cap = (int32_t)(std::ceil((1.5 * m + 32.0) / 16.0) * 16.0);
+  }
+  cudaFree(A.nbr);
+  cudaFree(A.nnbr);
+  cudaFree(A.xb);
+  cudaFree((void*)A.cell_box_v);
+  A.nbr = nullptr;
+  A.nnbr = nullptr;
+  A.xb = nullptr;
+  A.cell_box_v = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto M = [&](auto*& p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p, bytes);
+  };
+  M(A.nbr, sizeof(int32_t) * (size_t)n * cap);
+  M(A.nnbr, sizeof(int32_t) * n);
+  M(A.xb, sizeof(uint32_t) * 3 * n);
+  uint16_t* cbv = nullptr;
+  M(cbv, sizeof(uint16_t) * ncv);
+  A.cell_box_v = cbv;
+  if (!A.since_build) M(A.since_build, sizeof(uint32_t) * 2);
+  A.skin_flag = A.since_build ? A.since_build + 1 : nullptr;
+  if (ncv > E.ncells) {  // the cell arrays serve both grids
+    cudaFree(A.cnt);
+    cudaFree(A.cell_start);
+    cudaFree(A.scan_tot);
+    A.cnt = A.cell_start = A.scan_tot = nullptr;
+    M(A.cnt, sizeof(uint32_t) * (ncv + 1));
+    M(A.cell_start, sizeof(uint32_t) * (ncv + 1));
+    M(A.scan_tot, sizeof(uint32_t) * (ncv / 256 + 64));
+    E.ncells = ncv;
+  }
+  if (e != cudaSuccess) {
+    E.err = "out of device memory for the Verlet lists";
+    A.vl = 0;
+    return LJ_ERR_OOM;
+  }
+  std::vector<uint16_t> hcb(ncv);
+  for (int b = 0; b < E.nboxes; ++b) {
+    const EnsBox& B = E.hb[b];
+    const int64_t m = (int64_t)B.ncv * B.ncv * B.ncv;
+    for (int64_t c = 0; c < m; ++c) hcb[B.cell_off_v + c] = (uint16_t)b;
+  }
+  const uint32_t words[2] = {0x40000000u, 0u};  // build at the next step; no skin event
+  e = cudaMemcpyAsync(cbv, hcb.data(), sizeof(uint16_t) * ncv, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.since_build, words, sizeof(words), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync((void*)A.boxes, E.hb.data(), sizeof(EnsBox) * E.nboxes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    E.err = cudaGetErrorString(e);
+    return LJ_ERR_CUDA;
+  }
+  A.vl = 1;
+  A.rebuild_every = rebuild_every;
+  A.cap = cap;
+  A.ncells_v = ncv;
+  E.skin = skin;
+  E.forces_valid = false;
+  if (E.gexec) {  // the captured graph holds the old arguments
+    cudaGraphExecDestroy(E.gexec);
+    cudaGraphDestroy(E.graph);
+    E.gexec = nullptr;
+    E.graph = nullptr;
+  }
+  return LJ_OK;
 }
 
 // Copies the state out (host arrays, boxes concatenated; within box b the
@@ -809,7 +1080,8 @@ void lj_ensemble_destroy(lj_ens* h) {
   if (E.graph) cudaGraphDestroy(E.graph);
   EnsArgs& A = E.A;
   void* ps[] = {(void*)A.boxes, (void*)A.box_of, A.pos, A.pos_alt, A.vel, A.vel_alt, A.frc, A.frc_alt, A.cnt,
-                A.cell_start, A.cell_of, A.slot, A.key, A.key2, A.scan_tot, A.bar, A.status, A.npairs};
+                A.cell_start, A.cell_of, A.slot, A.key, A.key2, A.scan_tot, A.bar, A.status, A.npairs,
+                A.nbr, A.nnbr, A.xb, (void*)A.cell_box_v, A.since_build};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (E.own_stream) cudaStreamDestroy(E.stream);

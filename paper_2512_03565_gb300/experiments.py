@@ -13,7 +13,7 @@
   configuration in hindsight (from the full-search evidence of every phase).
 
 * ``ensemble``: the 256-box batch in one persistent launch vs the same boxes
-  run one after another.
+  run one after another, on linked cells and on Verlet lists.
 
 * ``energy``: time and energy per evaluation of every configuration on four
   systems, and whether the runtime-best and energy-best choices differ.
@@ -144,15 +144,19 @@ def droplet(radius=84.19, steps=10000, phase=500, samples=3, arms=("exhaustive",
     return out
 
 
-def ensemble(nboxes=256, steps=1000, dt=0.002, seq_boxes=None, log=print):
+def ensemble(nboxes=256, steps=1000, dt=0.002, seq_boxes=None, lists=False, log=print):
     """The batched ensemble: `nboxes` boxes (N log-uniform in [500, 50000], rho
     uniform in [0.1, 1.0]) for `steps` steps in one persistent launch per run,
     replayed as a CUDA graph, after the launch-shape autotuner; compared with
-    the same boxes integrated one after another through the single-box path."""
+    the same boxes integrated one after another through the single-box path.
+    lists=True runs the batch on Verlet lists (skin 0.3, rebuilt every 10
+    steps inside the launch) and the single-box runs on the same list order."""
     boxes = W.config5(nboxes)
     ntot = sum(s.n for s in boxes)
-    log(f"ensemble: {nboxes} boxes, {ntot} particles")
+    log(f"ensemble: {nboxes} boxes, {ntot} particles, {'Verlet lists' if lists else 'linked cells'}")
     ens = lj.Ensemble(boxes)
+    if lists:
+        ens.set_lists(0.3, 10)
     w, blk = ens.tune(dt, 10)
     ens.run(dt, 0)                   # initial forces
     ens.run(dt, 10)                  # warm-up, capture
@@ -165,10 +169,11 @@ def ensemble(nboxes=256, steps=1000, dt=0.002, seq_boxes=None, log=print):
     ens.close()
     seq = list(range(len(boxes))) if seq_boxes is None else list(seq_boxes)
     t_seq, n_seq = 0.0, 0
-    cfg = lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, w)
+    cfg = lj.config(lj.LJ_VL if lists else lj.LJ_LC, lj.LJ_ORD_JSPLIT, w)
+    edge = 2.8 if lists else 2.5
     for k in seq:
         s = boxes[k]
-        if int(np.floor(s.L / s.rc)) < 3:
+        if int(np.floor(s.L / edge)) < 3:
             continue                 # the single-box path needs >= 3 cells per axis
         d = lj.Domain(s.L, s.rc, s.skin)
         d.set_particles(s.pos, s.vel)
@@ -180,7 +185,7 @@ def ensemble(nboxes=256, steps=1000, dt=0.002, seq_boxes=None, log=print):
         t_seq += time.perf_counter() - t0
         n_seq += s.n
         d.close()
-    out = {"boxes": nboxes, "particles": ntot, "steps": steps, "w": w, "block": blk, "graph": graph,
+    out = {"boxes": nboxes, "particles": ntot, "steps": steps, "lists": lists, "w": w, "block": blk, "graph": graph,
            "ensemble_s": t_ens, "pairs_per_s": pairs / t_ens, "particle_steps_per_s": ntot * steps / t_ens,
            "sequential_s": t_seq, "sequential_particles": n_seq,
            "sequential_particle_steps_per_s": n_seq * steps / t_seq if t_seq else None}
@@ -252,7 +257,7 @@ def main(argv=None):
             if a.out:
                 json.dump(summ, open(a.out, "w"))
     elif a.what == "ensemble":
-        res = ensemble(steps=a.steps)
+        res = {"linked_cells": ensemble(steps=a.steps), "verlet_lists": ensemble(steps=a.steps, lists=True)}
         if a.out:
             json.dump(res, open(a.out, "w"))
     elif a.what == "energy":

@@ -97,6 +97,7 @@ _SIGS = {
     "lj_bin_cells_static": (C.c_int, [_VP, C.c_int64, C.c_int32, _VP, _VP, _VP]),
     "lj_ensemble_create": (C.c_int, [C.POINTER(_VP), C.c_int32, _VP, _VP, _VP, _VP, C.c_double, C.c_double,
                                      C.c_double, C.c_double, _VP]),
+    "lj_ensemble_set_lists": (C.c_int, [_VP, C.c_double, C.c_int32, C.c_int32]),
     "lj_ensemble_run": (C.c_int, [_VP, C.c_double, C.c_int32, C.c_int32]),
     "lj_ensemble_tune": (C.c_int, [_VP, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lj_ensemble_get": (C.c_int, [_VP, _VP, _VP, _VP]),
@@ -368,6 +369,12 @@ class Ensemble:
         st = self.lib.lj_ensemble_run(self.h, dt, nsteps, int(bool(use_graph)))
         if st != LJ_OK:
             raise LJError(st, "lj_ensemble_run failed")
+
+    def set_lists(self, skin=0.3, rebuild_every=10, cap=0):
+        """Verlet-list mode (skin > 0) or linked cells (skin = 0) for the batch."""
+        st = self.lib.lj_ensemble_set_lists(self.h, float(skin), int(rebuild_every), int(cap))
+        if st != LJ_OK:
+            raise LJError(st, self.lib.lj_ensemble_last_error(self.h).decode())
 
     def tune(self, dt=0.002, steps=10):
         w, b = C.c_int32(), C.c_int32()

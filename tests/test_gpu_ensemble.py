@@ -106,3 +106,66 @@ def test_ensemble_barrier_timeout_is_reported(lj):
     ens.debug(0, -1)
     ens.run(0.002, 3)
     ens.close()
+
+
+def test_ensemble_lists_initial_forces_match_oracle(lj):
+    """Verlet-list mode: the lists built inside the launch (one warp per cell;
+    whole-box lists for the box with fewer than 3 cells of edge r_c + skin)
+    give the oracle's forces."""
+    boxes = small_ensemble(seed=21)
+    assert any(int(np.floor(s.L / 2.8)) < 3 for s in boxes)
+    ens = lj.Ensemble(boxes)
+    ens.set_lists(0.3, 10)
+    ens.run(0.002, 0)
+    for s, (pos, vel, frc) in zip(boxes, ens.state()):
+        assert np.array_equal(pos, s.pos)
+        F_ref, _, _, _ = oracle.forces_bruteforce(s.pos, s.L, 2.5)
+        assert rel_err(frc, F_ref) <= 1e-5
+    ens.close()
+
+
+def test_ensemble_lists_match_single_box_list_runs(lj):
+    """25 steps with list rebuilds at steps 10 and 20 inside the launch: each
+    box follows the single-box Verlet-list path (same lists, same JSPLIT order
+    and width) to rounding, and its final forces match the oracle's."""
+    boxes = small_ensemble(seed=23)
+    ens = lj.Ensemble(boxes)
+    ens.set_lists(0.3, 10)
+    ens.run(0.002, 25, use_graph=True)
+    assert ens.uses_graph(), ens.last_error()
+    w = 8
+    for s, (pos, vel, frc) in zip(boxes, ens.state()):
+        if int(np.floor(s.L / 2.8)) >= 3:
+            d = lj.Domain(s.L, 2.5, 0.3)
+            d.set_particles(s.pos, s.vel)
+            d.integrate(0.002, 25, lj.config(lj.LJ_VL, lj.LJ_ORD_JSPLIT, w), rebuild_every=10)
+            p_ref, v_ref = d.state()
+            d.close()
+            dp = np.abs(pos.astype(np.int64) - p_ref.astype(np.int64))
+            assert np.minimum(dp, 2 ** 32 - dp).max() <= 64
+        F_orc, _, _, _ = oracle.forces_bruteforce(pos, s.L, 2.5)
+        assert rel_err(frc, F_orc) <= 1e-5
+    ens.close()
+
+
+def test_ensemble_lists_skin_rebuild(lj):
+    """A particle moving 4 sigma per step leaves its skin in the first step:
+    the launch rebuilds the lists before that step's forces, which match the
+    oracle's (missing pairs of the moved particle would not)."""
+    boxes = small_ensemble(nboxes=4, seed=25)
+    vel = boxes[0].vel.copy()
+    vel[:, 3] = [2000.0, 0.0, 0.0]
+    boxes[0] = W.System(L=boxes[0].L, pos=boxes[0].pos, vel=vel, name="teleport")
+    ens = lj.Ensemble(boxes)
+    ens.set_lists(0.3, 1000)
+    ens.run(0.002, 0)
+    ens.run(0.002, 1)
+    for s, (pos, _, frc) in zip(boxes, ens.state()):
+        F_orc, _, _, _ = oracle.forces_bruteforce(pos, s.L, 2.5)
+        assert rel_err(frc, F_orc) <= 1e-5
+    ens.set_lists(0.0)                            # back to linked cells
+    ens.run(0.002, 2)
+    for s, (pos, _, frc) in zip(boxes, ens.state()):
+        F_orc, _, _, _ = oracle.forces_bruteforce(pos, s.L, 2.5)
+        assert rel_err(frc, F_orc) <= 1e-5
+    ens.close()
