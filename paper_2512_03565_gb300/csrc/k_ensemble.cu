@@ -350,7 +350,7 @@ __device__ __forceinline__ void ens_build_lists(const EnsArgs& A, const uint4* _
   }
 }
 
-template <int W>
+template <int W, bool VL>
 __global__ void k_ensemble(EnsArgs A) {
   unsigned gen = 0;
   const int64_t n = A.ntot;
@@ -379,7 +379,7 @@ __global__ void k_ensemble(EnsArgs A) {
           pc[a] += (uint32_t)__double2loint(__fma_rn(v, dtu, M));
         }
         pos[i] = p;
-        if (A.vl) {
+        if (VL) {
           const int a = (int)(p.x - A.xb[i]), b = (int)(p.y - A.xb[n + i]), c = (int)(p.z - A.xb[2 * n + i]);
           const uint64_t d2 = (uint64_t)((long long)a * a) + (uint64_t)((long long)b * b) +
                               (uint64_t)((long long)c * c);
@@ -387,17 +387,17 @@ __global__ void k_ensemble(EnsArgs A) {
         }
       }
     }
-    if (A.vl && blockIdx.x == 0 && threadIdx.x == 0) *A.since_build += 1u;
+    if (VL && blockIdx.x == 0 && threadIdx.x == 0) *A.since_build += 1u;
     // linked cells rebin every step; lists are rebuilt on schedule or when a
     // particle left its skin (every block reads the same words after the barrier)
-    if (!A.vl)
+    if (!VL)
       for (int64_t c = tid; c < A.ncells; c += nthr) A.cnt[c] = 0u;
     if (!ens_barrier(A, gen)) return;
-    const bool rebuild = !A.vl || *((volatile uint32_t*)A.since_build) >= (uint32_t)A.rebuild_every ||
+    const bool rebuild = !VL || *((volatile uint32_t*)A.since_build) >= (uint32_t)A.rebuild_every ||
                          *((volatile uint32_t*)A.skin_flag) != 0u;
-    const int64_t ncells = A.vl ? A.ncells_v : A.ncells;
+    const int64_t ncells = VL ? A.ncells_v : A.ncells;
     if (rebuild) {
-    if (A.vl) {
+    if (VL) {
       for (int64_t c = tid; c < ncells; c += nthr) A.cnt[c] = 0u;
       if (!ens_barrier(A, gen)) return;
     }
@@ -405,8 +405,8 @@ __global__ void k_ensemble(EnsArgs A) {
     for (int64_t i = tid; i < n; i += nthr) {
       const EnsBox& B = A.boxes[A.box_of[i]];
       const uint4 p = pos[i];
-      const uint32_t nc = (uint32_t)(A.vl ? B.ncv : B.nc);
-      const uint32_t c = (uint32_t)(A.vl ? B.cell_off_v : B.cell_off) +
+      const uint32_t nc = (uint32_t)(VL ? B.ncv : B.nc);
+      const uint32_t c = (uint32_t)(VL ? B.cell_off_v : B.cell_off) +
                          (cx_of(p.z, nc) * nc + cx_of(p.y, nc)) * nc + cx_of(p.x, nc);
       A.cell_of[i] = c;
       A.slot[i] = atomicAdd(&A.cnt[c], 1u);
@@ -477,7 +477,7 @@ __global__ void k_ensemble(EnsArgs A) {
       double* tf = frc; frc = frc2; frc2 = tf;
     }
     if (!ens_barrier(A, gen)) return;
-    if (A.vl) {
+    if (VL) {
       // ---- list build; a list beyond the capacity stops the run
       ens_build_lists(A, pos, A.cell_start);
       if (!ens_barrier(A, gen)) return;
@@ -489,7 +489,7 @@ __global__ void k_ensemble(EnsArgs A) {
     }
     }  // rebuild
     // ---- forces, then the closing kick of this step
-    if (A.vl)
+    if (VL)
       ens_forces_vl<W>(A, pos, frc);
     else
       ens_forces<W>(A, pos, A.cell_start, frc);
@@ -560,10 +560,10 @@ uint64_t ens_cut2(double L, double r) {
   return (uint64_t)q;
 }
 
-template <int W>
+template <int W, bool VL>
 cudaError_t ens_grid_w(int block, int& grid) {
   int per_sm = 0, dev = 0, sms = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble<W>, block, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble<W, VL>, block, 0);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -574,7 +574,7 @@ cudaError_t ens_grid_w(int block, int& grid) {
 
 // Cooperative launch (all blocks resident) through cudaLaunchKernelEx, which
 // stream capture records as a cooperative kernel node.
-template <int W>
+template <int W, bool VL>
 cudaError_t ens_launch_w(Ens& E, int grid) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -586,28 +586,36 @@ cudaError_t ens_launch_w(Ens& E, int grid) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_ensemble<W>, E.A);
+  return cudaLaunchKernelEx(&cfg, k_ensemble<W, VL>, E.A);
 }
 
-cudaError_t ens_grid(Ens& E, int& grid) {
+template <bool VL>
+cudaError_t ens_grid_v(Ens& E, int& grid) {
   switch (E.W) {
-    case 2: return ens_grid_w<2>(E.block, grid);
-    case 4: return ens_grid_w<4>(E.block, grid);
-    case 16: return ens_grid_w<16>(E.block, grid);
-    case 32: return ens_grid_w<32>(E.block, grid);
-    default: return ens_grid_w<8>(E.block, grid);
+    case 2: return ens_grid_w<2, VL>(E.block, grid);
+    case 4: return ens_grid_w<4, VL>(E.block, grid);
+    case 16: return ens_grid_w<16, VL>(E.block, grid);
+    case 32: return ens_grid_w<32, VL>(E.block, grid);
+    default: return ens_grid_w<8, VL>(E.block, grid);
   }
 }
 
-cudaError_t ens_launch(Ens& E, int grid) {
+template <bool VL>
+cudaError_t ens_launch_v(Ens& E, int grid) {
   switch (E.W) {
-    case 2: return ens_launch_w<2>(E, grid);
-    case 4: return ens_launch_w<4>(E, grid);
-    case 16: return ens_launch_w<16>(E, grid);
-    case 32: return ens_launch_w<32>(E, grid);
-    default: return ens_launch_w<8>(E, grid);
+    case 2: return ens_launch_w<2, VL>(E, grid);
+    case 4: return ens_launch_w<4, VL>(E, grid);
+    case 16: return ens_launch_w<16, VL>(E, grid);
+    case 32: return ens_launch_w<32, VL>(E, grid);
+    default: return ens_launch_w<8, VL>(E, grid);
   }
 }
+
+// Linked-cell and Verlet-list batches are separate instantiations, so that the
+// linked-cell kernel carries none of the list code (registers, occupancy).
+cudaError_t ens_grid(Ens& E, int& grid) { return E.A.vl ? ens_grid_v<true>(E, grid) : ens_grid_v<false>(E, grid); }
+
+cudaError_t ens_launch(Ens& E, int grid) { return E.A.vl ? ens_launch_v<true>(E, grid) : ens_launch_v<false>(E, grid); }
 
 }  // namespace
 
@@ -915,6 +923,12 @@ lj_status lj_ensemble_set_lists(lj_ens* h, double skin, int32_t rebuild_every, i
   Ens& E = h->e;
   EnsArgs& A = E.A;
   cudaStream_t s = E.stream;
+  if (E.gexec) {  // a captured graph holds the old mode and arguments
+    cudaGraphExecDestroy(E.gexec);
+    cudaGraphDestroy(E.graph);
+    E.gexec = nullptr;
+    E.graph = nullptr;
+  }
   if (skin == 0.0) {  // back to linked cells
     A.vl = 0;
     E.skin = 0.0;
@@ -996,12 +1010,6 @@ lj_status lj_ensemble_set_lists(lj_ens* h, double skin, int32_t rebuild_every, i
   A.ncells_v = ncv;
   E.skin = skin;
   E.forces_valid = false;
-  if (E.gexec) {  // the captured graph holds the old arguments
-    cudaGraphExecDestroy(E.gexec);
-    cudaGraphDestroy(E.graph);
-    E.gexec = nullptr;
-    E.graph = nullptr;
-  }
   return LJ_OK;
 }
 
