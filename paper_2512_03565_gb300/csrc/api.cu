@@ -149,6 +149,7 @@ lj_status need_particles(Ctx& c) {
 lj_status alloc_particles(Ctx& c, int64_t n) {
   if (n == c.n && c.pos) return LJ_OK;
   CK(dalloc(c.pos, n));
+  CK(dalloc(c.inv, n));
   CK(dalloc(c.pos_alt, n));
   CK(dalloc(c.vel, 3 * n));
   CK(dalloc(c.vel_alt, 3 * n));
@@ -170,6 +171,7 @@ lj_status alloc_particles(Ctx& c, int64_t n) {
 
 void reset_state_flags(Ctx& c) {
   c.kick_pending = false;  // new particles: nothing of the last step is due
+  c.skin_pending = false;
   c.binned_nc = 0;
   c.binned_for = -1;
   c.vl_valid = false;
@@ -206,6 +208,7 @@ int initial_cap(const Ctx& c, int half) {
 
 // Bins on the r_c + skin cells and builds the lists (regrowing on overflow).
 lj_status do_build_verlet(Ctx& c, int half, int colmajor, bool twopass) {
+  c.skin_pending = false;  // the new lists make an earlier skin check moot
   CKS(do_bin(c, LJ_VL));
   if (c.vl_cap == 0 || !c.nbr) {
     c.vl_cap = initial_cap(c, half);
@@ -375,9 +378,31 @@ lj_status run_force(Ctx& c, const lj_config& cfg, bool ev, bool acc_zeroed = fal
 lj_status force_eval(Ctx& c, const lj_config& cfg, double* energy, double* virial) {
   if (!order_is_valid(cfg)) return fail(c, LJ_ERR_ARG, "invalid configuration");
   CKS(need_particles(c));
-  CKS(prepare(c, cfg, false));
   const bool ev = energy || virial;
-  CKS(run_force(c, cfg, ev));
+  const bool twopass = cfg.newton3 == LJ_N3_TWOPASS;
+  if (c.skin_pending && cfg.container == LJ_VL && c.vl_valid && c.binned_for == LJ_VL &&
+      c.vl_half == (cfg.newton3 != LJ_N3_OFF ? 1 : 0) && c.vl_colmajor == (cfg.order == LJ_ORD_VL_IPT ? 1 : 0) &&
+      (!twopass || c.rev_valid)) {
+    // positions came from lj_update_positions, whose kernel checked the skin:
+    // evaluate on the current lists at once and read the flag meanwhile; if a
+    // particle left its skin, rebuild and evaluate again
+    c.skin_pending = false;
+    c.P.nc = c.nc_vl;
+    CKS(run_force(c, cfg, ev));
+    CK(cudaEventSynchronize(c.drift_done));
+    if (*reinterpret_cast<volatile uint32_t*>(c.skin_host)) {
+      c.counters[3] += 1;
+      CK(cudaMemsetAsync(c.status, 0, sizeof(uint32_t), c.stream));  // the speculative run's status is void
+      CKS(do_build_verlet(c, cfg.newton3 != LJ_N3_OFF ? 1 : 0, cfg.order == LJ_ORD_VL_IPT ? 1 : 0, twopass));
+      c.moved_since_build = false;
+      c.P.nc = c.nc_vl;
+      CKS(run_force(c, cfg, ev));
+    }
+  } else {
+    c.skin_pending = false;
+    CKS(prepare(c, cfg, false));
+    CKS(run_force(c, cfg, ev));
+  }
   c.last_cfg = cfg;
   if (ev) {
     CK(cudaMemcpyAsync(c.host_ev, c.ev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -509,7 +534,8 @@ static lj_status set_particles_impl(lj_ctx* h, int64_t n, const void* pos, bool 
   }
   cudaError_t e = fixed ? launch_load_fp((const uint32_t*)dpos, n, dvel, c.pos, c.vel, c.stream)
                         : launch_quantize((const double*)dpos, n, c.L, dvel, c.pos, c.vel, c.stream);
-  c.launches += 1;
+  if (e == cudaSuccess) e = launch_iota(c.inv, n, c.stream);
+  c.launches += 2;
   if (e == cudaSuccess) e = cudaMemsetAsync(c.frc, 0, 3 * (size_t)n * sizeof(double), c.stream);
   CK(e);
   c.mass = mass;
@@ -530,6 +556,17 @@ lj_status lj_set_particles_fp(lj_ctx* h, int64_t n, const uint32_t* pos_fp, cons
   return set_particles_impl(h, n, pos_fp, true, vel, mass, on_device);
 }
 
+// Device address of a host pointer the GPU can read and write directly (the
+// caller's pinned memory, mapped in the unified address space), or nullptr.
+static void* host_mapped(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 lj_status lj_update_positions(lj_ctx* h, const double* pos, int32_t on_device) {
   if (!h || !pos) return LJ_ERR_ARG;
   Ctx& c = h->c;
@@ -537,7 +574,10 @@ lj_status lj_update_positions(lj_ctx* h, const double* pos, int32_t on_device) {
   CKS(settle_kick(c));  // the pending kick belongs to the state being replaced
   const size_t pbytes = 3 * (size_t)c.n * sizeof(double);
   const double* dpos = pos;
-  if (!on_device) {
+  const double* mapped = on_device ? nullptr : (const double*)host_mapped(pos);
+  if (mapped) {
+    dpos = mapped;  // read by the kernel across the host link, no staging copy
+  } else if (!on_device) {
     if (c.stage_bytes < pbytes) {
       dfree(c.stage);
       c.stage = nullptr;
@@ -548,7 +588,14 @@ lj_status lj_update_positions(lj_ctx* h, const double* pos, int32_t on_device) {
     CK(cudaMemcpyAsync(c.stage, pos, pbytes, cudaMemcpyHostToDevice, c.stream));
     dpos = (const double*)c.stage;
   }
-  CK(launch_update_pos(c.pos, dpos, c.n, c.L, c.stream));
+  // with current lists the update kernel also checks the skin (mapped flag)
+  const bool check = c.vl_valid && c.binned_for == LJ_VL;
+  const double hs = 0.5 * c.skin * 4294967296.0 / c.L;
+  const uint64_t d2max = hs * hs >= 1.8e19 ? ~0ull : (uint64_t)(hs * hs);
+  if (check) *reinterpret_cast<volatile uint32_t*>(c.skin_host) = 0u;
+  CK(launch_update_pos(c.pos, c.inv, dpos, c.n, c.L, check ? c.x_build : nullptr, d2max, c.skin_dev, c.stream));
+  if (check) CK(cudaEventRecord(c.drift_done, c.stream));
+  c.skin_pending = check;
   c.launches += 1;
   // the cell order and the lists stay; the next evaluation rebins (linked
   // cells) or checks the skin and rebuilds only when needed (Verlet lists)
@@ -600,6 +647,7 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
   const double hdtm = 0.5 * dt / c.mass;
   const double dtu = dt * 4294967296.0 / c.L;
   const bool vl = cfg.container == LJ_VL;
+  c.skin_pending = false;  // the steps below check the skin themselves
   if (!c.forces_valid || memcmp(&c.last_cfg, &cfg, sizeof(cfg)) != 0) {
     CKS(prepare(c, cfg, false));
     CKS(run_force(c, cfg, false));
@@ -666,10 +714,14 @@ lj_status lj_get_forces(lj_ctx* h, double* dst, int32_t on_device) {
   CKS(need_particles(c));
   if (!c.forces_valid) return fail(c, LJ_ERR_STATE, "no forces computed");
   if (on_device) {
-    CK(launch_to_original(c.pos, c.frc, c.n, dst, c.stream));
+    CK(launch_from_slots(c.inv, c.frc, c.n, dst, c.stream));
     return LJ_OK;
   }
-  CK(launch_to_original(c.pos, c.frc, c.n, c.frc_alt, c.stream));
+  if (double* mapped = (double*)host_mapped(dst)) {  // written by the kernel across the host link
+    CK(launch_from_slots(c.inv, c.frc, c.n, mapped, c.stream));
+    return take_status(c);
+  }
+  CK(launch_from_slots(c.inv, c.frc, c.n, c.frc_alt, c.stream));
   CK(cudaMemcpyAsync(dst, c.frc_alt, 3 * (size_t)c.n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   return take_status(c);
 }
@@ -887,7 +939,7 @@ void lj_destroy(lj_ctx* h) {
   if (!h) return;
   Ctx& c = h->c;
   cudaStreamSynchronize(c.stream);
-  void* dev[] = {c.pos, c.pos_alt, c.vel, c.vel_alt, c.frc, c.frc_alt, c.cell_start, c.cnt, c.cell_of, c.slot,
+  void* dev[] = {c.pos, c.inv, c.pos_alt, c.vel, c.vel_alt, c.frc, c.frc_alt, c.cell_start, c.cnt, c.cell_of, c.slot,
                  c.key, c.scan_tmp, c.tiles, c.row_tiles, c.nbr, c.nnbr, c.x_build, c.maxlen, c.twopass,
                  c.rev_cnt, c.rev_start, c.rev_slot, c.rev_key, c.rev_key2, c.ev, c.status,
                  c.feat_stats, c.tile_ctr, c.stage, c.nbr16};

@@ -40,12 +40,32 @@ __global__ void k_quantize(const double* __restrict__ pos, int64_t n, double L, 
 }
 
 // New coordinates in the caller's order written into the current (cell)
-// order: slot s takes those of its particle pos[s].w, quantised as above.
-__global__ void k_update_pos(uint4* __restrict__ pos, const double* __restrict__ x, int64_t n, double L) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const uint32_t o = pos[s].w;
-  pos[s] = make_uint4(quantize_coord(x[o], L), quantize_coord(x[n + o], L), quantize_coord(x[2 * n + o], L), o);
+// order through the inverse permutation: particle o goes to slot inv[o],
+// quantised as above.  x is read in the caller's order (coalesced), so it may
+// also be the caller's pinned host memory read across the host link.
+// With xb, the displacement since the last list build is checked as in the
+// integrator's drift (skin/2) and a particle beyond it sets the mapped host
+// word skin_flag.
+__global__ void k_update_pos(uint4* __restrict__ pos, const uint32_t* __restrict__ inv, const double* __restrict__ x,
+                             int64_t n, double L, const uint32_t* __restrict__ xb, uint64_t disp2_max,
+                             uint32_t* skin_flag) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const uint32_t s = inv[o];
+  const uint4 p = make_uint4(quantize_coord(x[o], L), quantize_coord(x[n + o], L), quantize_coord(x[2 * n + o], L),
+                             (uint32_t)o);
+  pos[s] = p;
+  if (xb) {
+    const int a = (int)(p.x - xb[s]), b = (int)(p.y - xb[n + s]), c = (int)(p.z - xb[2 * n + s]);
+    const uint64_t d2 = (uint64_t)((long long)a * a) + (uint64_t)((long long)b * b) + (uint64_t)((long long)c * c);
+    if (d2 > disp2_max) *skin_flag = 1u;
+  }
+}
+
+// inv[o] = o: the order right after a load
+__global__ void k_iota(uint32_t* __restrict__ inv, int64_t n) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < n) inv[o] = (uint32_t)o;
 }
 
 __global__ void k_load_fp(const uint32_t* __restrict__ pos, int64_t n, const double* __restrict__ vel,
@@ -65,8 +85,14 @@ cudaError_t launch_quantize(const double* pos, int64_t n, double L, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_pos(uint4* pos, const double* x, int64_t n, double L, cudaStream_t s) {
-  k_update_pos<<<nblk(n, 256), 256, 0, s>>>(pos, x, n, L);
+cudaError_t launch_update_pos(uint4* pos, const uint32_t* inv, const double* x, int64_t n, double L,
+                              const uint32_t* xb, uint64_t disp2_max, uint32_t* skin_flag, cudaStream_t s) {
+  k_update_pos<<<nblk(n, 256), 256, 0, s>>>(pos, inv, x, n, L, xb, disp2_max, skin_flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iota(uint32_t* inv, int64_t n, cudaStream_t s) {
+  k_iota<<<nblk(n, 256), 256, 0, s>>>(inv, n);
   return cudaGetLastError();
 }
 
@@ -252,11 +278,13 @@ cudaError_t sort_segments(Ctx& c, const uint32_t* starts, int64_t nseg, unsigned
 
 __global__ void k_permute(const unsigned long long* __restrict__ key, int64_t n, const uint4* __restrict__ pos,
                           const double* __restrict__ vel, const double* __restrict__ frc, uint4* __restrict__ pos2,
-                          double* __restrict__ vel2, double* __restrict__ frc2) {
+                          double* __restrict__ vel2, double* __restrict__ frc2, uint32_t* __restrict__ inv) {
   int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= n) return;
   const uint32_t s = (uint32_t)(key[d] & 0xffffffffull);
-  pos2[d] = pos[s];
+  const uint4 p = pos[s];
+  pos2[d] = p;
+  inv[p.w] = (uint32_t)d;  // original index -> new slot
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     vel2[a * n + d] = vel[a * n + s];
@@ -287,7 +315,8 @@ cudaError_t bin_cells(Ctx& c, int nc) {
   k_scatter_keys<<<nblk(n, 256), 256, 0, c.stream>>>(c.pos, n, c.cell_of, c.slot, c.cell_start, c.key);
   unsigned long long* key2 = c.key + n;
   if ((e = sort_segments(c, c.cell_start, ncell, c.key, key2)) != cudaSuccess) return e;
-  k_permute<<<nblk(n, 256), 256, 0, c.stream>>>(key2, n, c.pos, c.vel, c.frc, c.pos_alt, c.vel_alt, c.frc_alt);
+  k_permute<<<nblk(n, 256), 256, 0, c.stream>>>(key2, n, c.pos, c.vel, c.frc, c.pos_alt, c.vel_alt, c.frc_alt,
+                                                 c.inv);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   std::swap(c.pos, c.pos_alt);
   std::swap(c.vel, c.vel_alt);

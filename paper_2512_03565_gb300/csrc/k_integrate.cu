@@ -88,6 +88,23 @@ __global__ void k_pos_to_original(const uint4* __restrict__ pos, int64_t n, uint
   dst[2 * n + p.w] = p.z;
 }
 
+// dst[a][o] = src[a][inv[o]]: writes in the caller's order (coalesced), so dst
+// may also be the caller's pinned host memory written across the host link.
+__global__ void k_from_slots(const uint32_t* __restrict__ inv, const double* __restrict__ src, int64_t n,
+                             double* __restrict__ dst) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const uint32_t s = inv[o];
+  dst[o] = src[s];
+  dst[n + o] = src[n + s];
+  dst[2 * n + o] = src[2 * n + s];
+}
+
+cudaError_t launch_from_slots(const uint32_t* inv, const double* src3, int64_t n, double* dst3, cudaStream_t s) {
+  k_from_slots<<<nb(n, 256), 256, 0, s>>>(inv, src3, n, dst3);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s) {
   k_to_original<<<nb(n, 256), 256, 0, s>>>(pos, src3, n, dst3);
   return cudaGetLastError();

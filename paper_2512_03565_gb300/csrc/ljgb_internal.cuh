@@ -309,6 +309,7 @@ struct Ctx {
 
   // particle state in the current (cell) order
   uint4* pos = nullptr;    // x, y, z fixed point, w = original index
+  uint32_t* inv = nullptr; // original index -> current slot (inverse of pos[].w)
   uint4* pos_alt = nullptr;
   double* vel = nullptr;   // [3][n]
   double* vel_alt = nullptr;
@@ -319,6 +320,9 @@ struct Ctx {
   // are at the half step and v += kick_hdtm * F is due (see lj_integrate_step)
   bool kick_pending = false;
   double kick_hdtm = 0.0;
+  // lj_update_positions checked the skin into skin_host (event drift_done):
+  // the next list evaluation runs at once and rebuilds only if it was exceeded
+  bool skin_pending = false;
 
   // binning
   int binned_nc = 0;       // n_c of the current cell order (0 = not binned)
@@ -423,7 +427,10 @@ cudaError_t excl_scan_u32(Ctx& c, const uint32_t* in, uint32_t* out, int64_t n);
 cudaError_t sort_segments(Ctx& c, const uint32_t* starts, int64_t nseg, unsigned long long* key,
                           unsigned long long* key2);
 cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen);
-cudaError_t launch_update_pos(uint4* pos, const double* x, int64_t n, double L, cudaStream_t s);
+cudaError_t launch_update_pos(uint4* pos, const uint32_t* inv, const double* x, int64_t n, double L,
+                              const uint32_t* xb, uint64_t disp2_max, uint32_t* skin_flag, cudaStream_t s);
+cudaError_t launch_iota(uint32_t* inv, int64_t n, cudaStream_t s);
+cudaError_t launch_from_slots(const uint32_t* inv, const double* src3, int64_t n, double* dst3, cudaStream_t s);
 cudaError_t launch_reverse_index(Ctx& c);
 cudaError_t launch_list_to16(Ctx& c, uint32_t* overflow);
 

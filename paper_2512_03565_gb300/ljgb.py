@@ -257,7 +257,8 @@ class Domain:
         return None
 
     def forces(self, out=None):
-        """Forces (3, n) float64 in original order; into `out` (device tensor) if given."""
+        """Forces (3, n) float64 in original order; into `out` (a device tensor, or a host tensor, written
+        directly by the kernel when pinned) if given."""
         if out is not None:
             p, dev, _ = _ptr(out, np.float64)
             self._check(self.lib.lj_get_forces(self.h, p, dev))

@@ -204,6 +204,17 @@ def test_update_positions_keeps_lists_while_the_skin_allows(lj):
         assert rel_err(d.forces(), F_orc) <= 1e-12
     pos, vel = d.state()
     assert np.array_equal(vel, s.vel)                           # velocities untouched
+    # the caller's pinned host memory is read and written by the kernels
+    # directly (no staging copies): same positions in, same forces out, bitwise
+    import torch
+    F_staged = d.forces()
+    x_pin = torch.from_numpy(np.ascontiguousarray(large)).pin_memory()
+    f_pin = torch.empty((3, s.n), dtype=torch.float64).pin_memory()
+    d.update_positions(x_pin)
+    d.compute_forces(cfg)
+    d.forces(out=f_pin)
+    assert np.array_equal(f_pin.numpy(), F_staged)
+    assert np.array_equal(d.state()[0], pos)
     d.close()
 
 
