@@ -287,7 +287,9 @@ def run_ours(args, ws, rank, local, pg):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel_ms": avg_force_s * 1e3,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FFMA)",
-            "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3]}
+            "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3],
+            # the kernel's own pair evaluations (Newton-3 off evaluates each pair from both sides)
+            "kernel_pair_evals_per_s": (2.0 if cfg.newton3 == 0 else 1.0) * float(np.mean(pairs)) / avg_force_s}
     if traffic:
         hbm_peak = 6800.0
         try:
