@@ -18,7 +18,9 @@
 * ``energy``: time and energy per evaluation of every configuration on four
   systems, and whether the runtime-best and energy-best choices differ.
 
-Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|energy [options]
+* ``ensemble-launch``: one direct launch of the list-mode batch (for ncu).
+
+Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy [options]
 """
 from __future__ import annotations
 
@@ -225,7 +227,7 @@ def energy(min_ms=1000.0, log=print):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "energy"])
+    ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--data", default="gpurun_out/tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
@@ -260,6 +262,16 @@ def main(argv=None):
         res = {"linked_cells": ensemble(steps=a.steps), "verlet_lists": ensemble(steps=a.steps, lists=True)}
         if a.out:
             json.dump(res, open(a.out, "w"))
+    elif a.what == "ensemble-launch":
+        # the 256-box batch on Verlet lists: an initial-force launch, then one
+        # direct (not graph-replayed) launch of a.steps steps, for profilers
+        ens = lj.Ensemble(W.config5(256))
+        ens.set_lists(0.3, 10)
+        ens.run(0.002, 0, use_graph=False)
+        t0 = time.perf_counter()
+        ens.run(0.002, a.steps, use_graph=False)
+        print(json.dumps({"steps": a.steps, "ms_per_step": (time.perf_counter() - t0) / max(1, a.steps) * 1e3}))
+        ens.close()
     elif a.what == "energy":
         res = energy()
         print(json.dumps({k: v for k, v in res.items() if k != "systems"}))
