@@ -90,8 +90,14 @@ typedef enum {
 /* Newton's third law (Sec. 2.1, Sec. 4.1.3): off (every pair evaluated from
  * both sides), on with the j contribution scattered by FP64 atomics, or on with
  * a deterministic two-pass reduction (j partials written to a buffer, then
- * gathered per particle in a fixed order; ROT32 on linked cells only). */
-typedef enum { LJ_N3_OFF = 0, LJ_N3_ATOMIC = 1, LJ_N3_TWOPASS = 2 } lj_newton3;
+ * gathered per particle in a fixed order; Verlet lists, VL_IPT only).
+ * LJ_N3_ATOMIC_BWD (linked cells only) is LJ_N3_ATOMIC with the roles of the
+ * two cells of every cell pair swapped: each i visits the backward half shell
+ * (the neighbour cells before its own in cell order) instead of the forward
+ * one.  The pair set is the same; which particles are loaded as i's and which
+ * receive the scattered j forces differs (the domain-traversal dimension of
+ * Sec. 5.1, where the two orders of a cell pair run at different speeds). */
+typedef enum { LJ_N3_OFF = 0, LJ_N3_ATOMIC = 1, LJ_N3_TWOPASS = 2, LJ_N3_ATOMIC_BWD = 3 } lj_newton3;
 
 typedef struct {
   int32_t container; /* lj_container */

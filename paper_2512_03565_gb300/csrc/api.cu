@@ -93,7 +93,7 @@ bool order_is_valid(const lj_config& g) {
       default:
         return false;
     }
-    return g.newton3 == LJ_N3_OFF || g.newton3 == LJ_N3_ATOMIC;
+    return g.newton3 == LJ_N3_OFF || g.newton3 == LJ_N3_ATOMIC || g.newton3 == LJ_N3_ATOMIC_BWD;
   }
   if (g.container == LJ_VL) {
     if (g.order == LJ_ORD_VL_IPT) return g.param == 0 && g.newton3 >= LJ_N3_OFF && g.newton3 <= LJ_N3_TWOPASS;
@@ -121,6 +121,13 @@ std::vector<lj_config> all_configs() {
     for (int w : {32, 16, 8, 4, 2}) v.push_back({LJ_VL, LJ_ORD_JSPLIT, w, n3});
   }
   v.push_back({LJ_VL, LJ_ORD_VL_IPT, 0, LJ_N3_TWOPASS});
+  // the backward half shell last, so that the indices above stay as they were
+  v.push_back({LJ_LC, LJ_ORD_IPT_SMEM, 0, LJ_N3_ATOMIC_BWD});
+  v.push_back({LJ_LC, LJ_ORD_IPT_TMA, 0, LJ_N3_ATOMIC_BWD});
+  v.push_back({LJ_LC, LJ_ORD_KI, 2, LJ_N3_ATOMIC_BWD});
+  v.push_back({LJ_LC, LJ_ORD_KI, 4, LJ_N3_ATOMIC_BWD});
+  for (int w : {32, 16, 8, 4, 2}) v.push_back({LJ_LC, LJ_ORD_JSPLIT, w, LJ_N3_ATOMIC_BWD});
+  v.push_back({LJ_LC, LJ_ORD_ROT32, 0, LJ_N3_ATOMIC_BWD});
   return v;
 }
 

@@ -197,7 +197,7 @@ __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __rest
       if (B.nc >= 3) {
         const int nc = B.nc;
         const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
-        ns = make_segments<false>(cs + B.cell_off, nc, cz * nc + cy, cx, cx, (uint32_t)i, segs);
+        ns = make_segments<false>(cs + B.cell_off, nc, cz * nc + cy, cx, cx, (uint32_t)i, (uint32_t)i + 1u, segs);
       } else {
         segs[0] = {(uint32_t)B.off, (uint32_t)(B.off + B.n), 0};
         ns = 1;

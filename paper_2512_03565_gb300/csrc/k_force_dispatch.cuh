@@ -16,7 +16,7 @@ inline unsigned grid_for(int64_t threads, int tpb, int per_sm) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-template <typename R, bool N3, bool EV>
+template <typename R, bool N3, bool EV, bool BWD>
 cudaError_t lc_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
   LCArgs A{c.pos, c.cell_start, c.tiles, c.row_tiles + (size_t)c.binned_nc * c.binned_nc, c.tile_ctr};
   cudaError_t e;
@@ -31,34 +31,34 @@ cudaError_t lc_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
   switch (cfg.order) {
     case LJ_ORD_IPT_SMEM:
       if ((e = prep(32)) != cudaSuccess) return e;
-      k_lc_ipt<R, 1, N3, EV><<<grid_for(n, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
+      k_lc_ipt<R, 1, N3, EV, BWD><<<grid_for(n, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
       break;
     case LJ_ORD_KI:
       if (cfg.param == 2) {
         if ((e = prep(64)) != cudaSuccess) return e;
-        k_lc_ipt<R, 2, N3, EV><<<grid_for(n / 2 + 32, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
+        k_lc_ipt<R, 2, N3, EV, BWD><<<grid_for(n / 2 + 32, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
       } else {
         if ((e = prep(128)) != cudaSuccess) return e;
-        k_lc_ipt<R, 4, N3, EV><<<grid_for(n / 4 + 32, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
+        k_lc_ipt<R, 4, N3, EV, BWD><<<grid_for(n / 4 + 32, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
       }
       break;
     case LJ_ORD_IPT_TMA:
       if ((e = prep(32)) != cudaSuccess) return e;
-      k_lc_tma<R, N3, EV><<<grid_for(n, TMA_WARPS * 32, 16), TMA_WARPS * 32, 0, c.stream>>>(c.P, A, out);
+      k_lc_tma<R, N3, EV, BWD><<<grid_for(n, TMA_WARPS * 32, 16), TMA_WARPS * 32, 0, c.stream>>>(c.P, A, out);
       break;
     case LJ_ORD_ROT32:
       if ((e = prep(32)) != cudaSuccess) return e;
-      k_lc_rot<R, N3, EV><<<grid_for(n, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
+      k_lc_rot<R, N3, EV, BWD><<<grid_for(n, 256, 8), 256, 0, c.stream>>>(c.P, A, out);
       break;
     case LJ_ORD_JSPLIT: {
       const int w = cfg.param;
       const int64_t thr = n * w;
       switch (w) {
-        case 32: k_lc_jsplit<R, 32, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
-        case 16: k_lc_jsplit<R, 16, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
-        case 8: k_lc_jsplit<R, 8, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
-        case 4: k_lc_jsplit<R, 4, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
-        default: k_lc_jsplit<R, 2, N3, EV><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+        case 32: k_lc_jsplit<R, 32, N3, EV, BWD><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+        case 16: k_lc_jsplit<R, 16, N3, EV, BWD><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+        case 8: k_lc_jsplit<R, 8, N3, EV, BWD><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+        case 4: k_lc_jsplit<R, 4, N3, EV, BWD><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+        default: k_lc_jsplit<R, 2, N3, EV, BWD><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
       }
       break;
     }
@@ -71,13 +71,15 @@ cudaError_t lc_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
 template <typename R>
 cudaError_t force_lc_t(Ctx& c, const lj_config& cfg, bool ev) {
   ForceOut out{c.frc, c.frc + c.n, c.frc + 2 * c.n, c.ev, c.npairs, c.status};
-  const bool n3 = cfg.newton3 == LJ_N3_ATOMIC;
+  const bool bwd = cfg.newton3 == LJ_N3_ATOMIC_BWD;
+  const bool n3 = cfg.newton3 == LJ_N3_ATOMIC || bwd;
   if (n3) {
     cudaError_t e = cudaMemsetAsync(c.frc, 0, 3 * (size_t)c.n * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
   }
-  if (n3) return ev ? lc_launch<R, true, true>(c, cfg, out) : lc_launch<R, true, false>(c, cfg, out);
-  return ev ? lc_launch<R, false, true>(c, cfg, out) : lc_launch<R, false, false>(c, cfg, out);
+  if (bwd) return ev ? lc_launch<R, true, true, true>(c, cfg, out) : lc_launch<R, true, false, true>(c, cfg, out);
+  if (n3) return ev ? lc_launch<R, true, true, false>(c, cfg, out) : lc_launch<R, true, false, false>(c, cfg, out);
+  return ev ? lc_launch<R, false, true, false>(c, cfg, out) : lc_launch<R, false, false, false>(c, cfg, out);
 }
 
 // Launch of a Verlet-list kernel with an L2 access-policy window over the

@@ -35,8 +35,9 @@
 namespace ljgb {
 
 // A contiguous range of j's in cell order.  kind 0: all lanes; kind 1: own
-// row of a Newton-3 half shell, lane uses j only if j > i; kind 2: wrap cell
-// of the own row, used only by lanes whose i sits in the last cell of the row.
+// row of a Newton-3 half shell, lane uses j only if j > i (j < i in the
+// backward shell); kind 2: wrap cell of the own row, used only by lanes whose
+// i sits in the last cell of the row (the first cell in the backward shell).
 struct Seg {
   uint32_t b, e;
   int kind;
@@ -71,12 +72,18 @@ __device__ __forceinline__ int row_segments(const uint32_t* __restrict__ cs, int
 
 // The j segments of an i-range in row (cy, cz) spanning cells cf..cl.
 // Full shell: the 9 rows (dz, dy) in {-1,0,1}^2 with x-cells cf-1..cl+1.
-// Half shell: the own row from the first i up to cell min(cl+1, nc-1) (kind 1),
-// the wrap cell 0 when cl = nc-1 (kind 2), and the 4 forward rows
-// (0,+1), (+1,-1), (+1,0), (+1,+1) with x-cells cf-1..cl+1.
-template <bool HALF>
+// Half shell (Newton-3), forward: the own row from the first i up to cell
+// min(cl+1, nc-1) with j > i (kind 1), the wrap cell 0 when cl = nc-1 (kind 2,
+// for the i's of cell nc-1), and the 4 forward rows (0,+1), (+1,-1), (+1,0),
+// (+1,+1) with x-cells cf-1..cl+1.  Backward (BWD) is its mirror, the same
+// pairs with the roles of the two cells of every pair swapped (the domain
+// traversal dimension of Sec. 5.1): the own row from cell max(cf-1, 0) up to
+// the tile's last i with j < i (kind 1), the wrap cell nc-1 when cf = 0 (kind 2,
+// for the i's of cell 0), and the 4 rows (0,-1), (-1,+1), (-1,0), (-1,-1).
+// end_i is one past the tile's last particle.
+template <bool HALF, bool BWD = false>
 __device__ __forceinline__ int make_segments(const uint32_t* __restrict__ cs, int nc, int row, int cf, int cl,
-                                             uint32_t first_i, Seg* segs) {
+                                             uint32_t first_i, uint32_t end_i, Seg* segs) {
   const int cy = row % nc, cz = row / nc;
   int ns = 0;
   if (!HALF) {
@@ -87,7 +94,7 @@ __device__ __forceinline__ int make_segments(const uint32_t* __restrict__ cs, in
         const int r = ((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc;
         ns += row_segments(cs, nc, r, cf - 1, cl + 1, segs + ns);
       }
-  } else {
+  } else if (!BWD) {
     const int64_t base = (int64_t)row * nc;
     const int last = min(cl + 1, nc - 1);
     segs[ns++] = {first_i, cs[base + last + 1], 1};
@@ -98,12 +105,26 @@ __device__ __forceinline__ int make_segments(const uint32_t* __restrict__ cs, in
       const int r = ((cz + fw[q][0] + nc) % nc) * nc + (cy + fw[q][1] + nc) % nc;
       ns += row_segments(cs, nc, r, cf - 1, cl + 1, segs + ns);
     }
+  } else {
+    const int64_t base = (int64_t)row * nc;
+    const int lo = max(cf - 1, 0);
+    segs[ns++] = {cs[base + lo], end_i, 1};
+    if (cf == 0) segs[ns++] = {cs[base + nc - 1], cs[base + nc], 2};
+    const int bw[4][2] = {{0, -1}, {-1, 1}, {-1, 0}, {-1, -1}};
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int r = ((cz + bw[q][0] + nc) % nc) * nc + (cy + bw[q][1] + nc) % nc;
+      ns += row_segments(cs, nc, r, cf - 1, cl + 1, segs + ns);
+    }
   }
   return ns;
 }
 
+template <bool BWD = false>
 __device__ __forceinline__ bool seg_ok(int kind, uint32_t j, uint32_t i, uint32_t cxi, int nc) {
-  return kind == 0 || (kind == 1 ? (j > i) : (cxi == (uint32_t)(nc - 1)));
+  if (kind == 0) return true;
+  if (BWD) return kind == 1 ? (j < i) : (cxi == 0u);
+  return kind == 1 ? (j > i) : (cxi == (uint32_t)(nc - 1));
 }
 
 // Add v (R) times scale to an FP64 array element with an atomic.
@@ -124,7 +145,7 @@ struct LCArgs {
 // IPT_SMEM (K = 1) and KI<K>: warp per row tile of <= 32 K particles, j
 // chunks of 32 staged in the warp's shared-memory slot.
 // ---------------------------------------------------------------------------
-template <typename R, int K, bool N3, bool EV>
+template <typename R, int K, bool N3, bool EV, bool BWD = false>
 __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut out) {
   __shared__ uint4 s_j[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -153,7 +174,7 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
     }
     R eu = 0, ew = 0;
     Seg segs[18];
-    const int ns = make_segments<N3>(A.cs, nc, (int)tile.z, cf, cl, tile.x, segs);
+    const int ns = make_segments<N3, BWD>(A.cs, nc, (int)tile.z, cf, cl, tile.x, tile.y, segs);
 #pragma unroll 1
     for (int s = 0; s < ns; ++s) {
       const Seg sg = segs[s];
@@ -170,7 +191,7 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
           R hx = 0, hy = 0, hz = 0;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            if (vi[k] && seg_ok(sg.kind, jidx, ii[k], cxi[k], nc)) {
+            if (vi[k] && seg_ok<BWD>(sg.kind, jidx, ii[k], cxi[k], nc)) {
               R af, bf, cf_;
               const R fac = Prec<R>::template pair<EV, true>(mimg(pi[k].x, pj.x), mimg(pi[k].y, pj.y),
                                                        mimg(pi[k].z, pj.z), P, af, bf, cf_, eu, ew, cnt);
@@ -276,7 +297,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-template <typename R, bool N3, bool EV>
+template <typename R, bool N3, bool EV, bool BWD = false>
 __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A, ForceOut out) {
   __shared__ __align__(128) uint4 s_j[TMA_WARPS][2][TMA_CH];
   __shared__ __align__(8) uint64_t s_bar[TMA_WARPS][2];
@@ -306,7 +327,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
     const uint32_t cxi = cx_of(pi.x, nc);
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
     Seg segs[18];
-    const int ns = make_segments<N3>(A.cs, nc, (int)tile.z, cf, cl, tile.x, segs);
+    const int ns = make_segments<N3, BWD>(A.cs, nc, (int)tile.z, cf, cl, tile.x, tile.y, segs);
     // flatten (segment, offset) into chunks; issue chunk c+1 while computing c
     int s_cur = 0;
     uint32_t o_cur = 0;
@@ -349,7 +370,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
         const uint4 pj = s_j[wib][buf][q];
         const uint32_t jidx = jb + q;
         R hx = 0, hy = 0, hz = 0;
-        if (vi && seg_ok(sg.kind, jidx, ii, cxi, nc)) {
+        if (vi && seg_ok<BWD>(sg.kind, jidx, ii, cxi, nc)) {
           R af, bf, cf_;
           const R fac = Prec<R>::template pair<EV, true>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af,
                                                    bf, cf_, eu, ew, cnt);
@@ -414,7 +435,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
 // ROT32: warp per row tile of <= 32 i's; each j chunk of <= 32 sits one per
 // lane and rotates by one lane per step (32 steps = the full 32 x 32 tile).
 // ---------------------------------------------------------------------------
-template <typename R, bool N3, bool EV>
+template <typename R, bool N3, bool EV, bool BWD = false>
 __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut out) {
   const int lane = threadIdx.x & 31;
   const int nc = P.nc;
@@ -435,7 +456,7 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
     const uint32_t cxi = cx_of(pi.x, nc);
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
     Seg segs[18];
-    const int ns = make_segments<N3>(A.cs, nc, (int)tile.z, cf, cl, tile.x, segs);
+    const int ns = make_segments<N3, BWD>(A.cs, nc, (int)tile.z, cf, cl, tile.x, tile.y, segs);
 #pragma unroll 1
     for (int s = 0; s < ns; ++s) {
       const Seg sg = segs[s];
@@ -447,7 +468,7 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
 #pragma unroll 4
         for (int r = 0; r < 32; ++r) {
           const uint32_t src = (uint32_t)((lane + r) & 31);
-          if (vi && src < m && seg_ok(sg.kind, jb + src, ii, cxi, nc)) {
+          if (vi && src < m && seg_ok<BWD>(sg.kind, jb + src, ii, cxi, nc)) {
             R af, bf, cf_;
             const R fac = Prec<R>::template pair<EV, true>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P,
                                                      af, bf, cf_, eu, ew, cnt);
@@ -499,7 +520,7 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
 // JSPLIT<W>: groups of W lanes per i (32/W i's per warp, consecutive in cell
 // order); every group walks its own i's 27-cell (or half-shell) segments.
 // ---------------------------------------------------------------------------
-template <typename R, int W, bool N3, bool EV>
+template <typename R, int W, bool N3, bool EV, bool BWD = false>
 __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __restrict__ pos,
                                                    const uint32_t* __restrict__ cs, ForceOut out) {
   constexpr int G = 32 / W;
@@ -515,7 +536,7 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
     const uint4 pi = vi ? pos[ii] : make_uint4(0, 0, 0, 0);
     const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
     Seg segs[18];
-    int ns = vi ? make_segments<N3>(cs, nc, cz * nc + cy, cx, cx, ii, segs) : 0;
+    int ns = vi ? make_segments<N3, BWD>(cs, nc, cz * nc + cy, cx, cx, ii, ii, segs) : 0;
     const int nsmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)ns);
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
 #pragma unroll 1
@@ -527,7 +548,7 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
 #pragma unroll 1
       for (uint32_t q = 0; q < tmax; ++q) {
         const uint32_t j = sg.b + q * W + sub;
-        if (j < sg.e && seg_ok(sg.kind, j, ii, (uint32_t)cx, nc)) {
+        if (j < sg.e && seg_ok<BWD>(sg.kind, j, ii, (uint32_t)cx, nc)) {
           const uint4 pj = pos[j];
           R af, bf, cf_;
           const R fac = Prec<R>::template pair<EV, true>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af,

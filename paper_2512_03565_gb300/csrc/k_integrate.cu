@@ -216,7 +216,7 @@ __global__ void k_lc_pairs(const uint4* __restrict__ pos, const uint32_t* __rest
   const uint4 pi = pos[i];
   const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
   Seg segs[18];
-  const int ns = make_segments<false>(cs, nc, cz * nc + cy, cx, cx, 0u, segs);
+  const int ns = make_segments<false>(cs, nc, cz * nc + cy, cx, cx, 0u, 0u, segs);
   for (int s = 0; s < ns; ++s)
     for (uint32_t j = segs[s].b; j < segs[s].e; ++j) {
       const uint4 pj = pos[j];

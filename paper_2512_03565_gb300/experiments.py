@@ -20,7 +20,11 @@
 
 * ``ensemble-launch``: one direct launch of the list-mode batch (for ncu).
 
-Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy [options]
+* ``traversal``: the linked-cell Newton-3 orders with the forward and the
+  backward half shell (the two roles a cell can take in a cell pair, Sec.
+  5.1) on homogeneous, slab and solid systems, in both pair precisions.
+
+Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy|traversal [options]
 """
 from __future__ import annotations
 
@@ -225,9 +229,39 @@ def energy(min_ms=1000.0, log=print):
     return out
 
 
+def traversal(n=500_000, samples=5, log=print):
+    """Sec. 5.1: the same pairs, with the roles of the two cells of every cell
+    pair swapped.  Full-search times (rebin included, as in tuning) of every
+    linked-cell order with the forward (LJ_N3_ATOMIC) and the backward
+    (LJ_N3_ATOMIC_BWD) half shell; the ratio backward / forward per order and
+    whether the best linked-cell configuration changes direction."""
+    systems = [W.stratified(n, 0.75, W.BASE_SEED + 81), W.slab(n, 0.8, 0.02, 0.5, W.BASE_SEED + 82),
+               W.slab(n, 0.8, 0.02, 0.2, W.BASE_SEED + 83), W.fcc(n, 1.0, W.BASE_SEED + 84)]
+    out = []
+    for s in systems:
+        for prec in (lj.LJ_PREC_FP32_ACC64, lj.LJ_PREC_FP64):
+            d = lj.Domain(s.L, s.rc, s.skin, precision=prec)
+            d.set_particles(s.pos, s.vel)
+            _, times = d.tune(0, samples)
+            d.close()
+            ratio = {}
+            for k, v in times.items():
+                if k.startswith("LC:") and k.endswith(":N3atomic"):
+                    ratio[k[3:-len(":N3atomic")]] = times[k[:-len("N3atomic")] + "N3bwd"] / v
+            lc = {k: v for k, v in times.items() if k.startswith("LC:") and not k.endswith("N3off")}
+            best_lc = min(lc, key=lc.get)
+            r = {"system": s.name, "n": s.n, "precision": prec, "bwd_over_fwd": ratio,
+                 "best_lc_n3": best_lc, "best_overall": min(times, key=times.get), "times_ms": times}
+            out.append(r)
+            log(f"{s.name} prec={prec}: best LC Newton-3 {best_lc}; bwd/fwd " +
+                " ".join(f"{k}={v:.3f}" for k, v in sorted(ratio.items())))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy"])
+    ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy",
+                                     "traversal"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--data", default="gpurun_out/tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
@@ -272,6 +306,10 @@ def main(argv=None):
         ens.run(0.002, a.steps, use_graph=False)
         print(json.dumps({"steps": a.steps, "ms_per_step": (time.perf_counter() - t0) / max(1, a.steps) * 1e3}))
         ens.close()
+    elif a.what == "traversal":
+        res = traversal()
+        if a.out:
+            json.dump(res, open(a.out, "w"))
     elif a.what == "energy":
         res = energy()
         print(json.dumps({k: v for k, v in res.items() if k != "systems"}))

@@ -28,7 +28,7 @@ STATUS_NAMES = ["LJ_OK", "LJ_ERR_ARG", "LJ_ERR_CUDA", "LJ_ERR_CAPACITY", "LJ_ERR
 LJ_PREC_FP64, LJ_PREC_FP32_ACC64 = 0, 1
 LJ_LC, LJ_VL = 0, 1
 LJ_ORD_IPT_SMEM, LJ_ORD_IPT_TMA, LJ_ORD_KI, LJ_ORD_JSPLIT, LJ_ORD_ROT32, LJ_ORD_VL_IPT = range(6)
-LJ_N3_OFF, LJ_N3_ATOMIC, LJ_N3_TWOPASS = 0, 1, 2
+LJ_N3_OFF, LJ_N3_ATOMIC, LJ_N3_TWOPASS, LJ_N3_ATOMIC_BWD = 0, 1, 2, 3
 ORDER_NAMES = ["IPT_SMEM", "IPT_TMA", "KI", "JSPLIT", "ROT32", "VL_IPT"]
 
 
@@ -50,7 +50,7 @@ def config_name(c: lj_config) -> str:
     cont = "LC" if c.container == LJ_LC else "VL"
     o = ORDER_NAMES[c.order] if 0 <= c.order < len(ORDER_NAMES) else f"ord{c.order}"
     p = f"-{c.param}" if c.param else ""
-    n3 = ["N3off", "N3atomic", "N3twopass"][c.newton3] if 0 <= c.newton3 <= 2 else f"n3={c.newton3}"
+    n3 = ["N3off", "N3atomic", "N3twopass", "N3bwd"][c.newton3] if 0 <= c.newton3 <= 3 else f"n3={c.newton3}"
     return f"{cont}:{o}{p}:{n3}"
 
 
