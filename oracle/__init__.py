@@ -82,6 +82,9 @@ def _load():
             "orc_vv_run": (i32, [i64, _U32P, _U32P, _U32P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                  _F64P, f64, f64, i32, f64, f64, f64, f64, i32, vp, vp]),
             "orc_features": (i32, [i64, _U32P, _U32P, _U32P, f64, f64, f64, _F64P]),
+            "orc_vcl_ntower": (i32, [i64, i32]),
+            "orc_vcl_order": (i64, [i64, _U32P, _U32P, _U32P, i32, _U32P, _U32P]),
+            "orc_vcl_lists": (i32, [i64, _U32P, _U32P, _U32P, _U32P, _U32P, f64, f64, i32, i32, _I32P, _I32P]),
             "orc_mlp_nparams": (i64, [i32]),
             "orc_mlp_forward": (None, [_F64P, i32, i64, _F64P, _F64P]),
             "orc_mlp_loss_grad": (f64, [_F64P, i32, i64, _F64P, _F64P, _F64P, _F64P]),
@@ -201,6 +204,40 @@ def verlet(pos, L, rl, nc, half, cap):
     if r < 0:
         raise ValueError("need at least 3 cells per dimension")
     return perm[:n], cs, nbr[:n], nnbr[:n], bool(r)
+
+
+def vcl_ntower(n, M) -> int:
+    """Towers per axis of the cluster grid (reading R5): the largest k >= 1 with k^3 M <= n."""
+    return int(_load().orc_vcl_ntower(int(n), int(M)))
+
+
+def vcl_order(pos, M):
+    """Cluster order (reading R5).  Returns (perm, cl_start): perm[k] is the
+    original index of the k-th particle in cluster order, cluster c holds
+    perm[cl_start[c]:cl_start[c+1]]."""
+    x, y, z = _soa(pos)
+    n = x.shape[0]
+    perm = np.zeros(n, dtype=np.uint32)
+    cls = np.zeros(n + 1, dtype=np.uint32)
+    ncl = _load().orc_vcl_order(n, x, y, z, int(M), perm, cls)
+    if ncl < 0:
+        raise ValueError("need n >= 1 and M >= 1")
+    return perm, cls[:ncl + 1].copy()
+
+
+def vcl_lists(pos, L, rl, M, half):
+    """Cluster-pair lists by brute force over all cluster pairs (reading R5).
+    Returns (perm, cl_start, lists): lists[I] the ascending neighbour clusters of I."""
+    x, y, z = _soa(pos)
+    perm, cls = vcl_order(pos, M)
+    ncl = cls.shape[0] - 1
+    nn = np.zeros(max(ncl, 1), dtype=np.int32)
+    cap = max(ncl, 1)
+    nbr = np.zeros((max(ncl, 1), cap), dtype=np.int32)
+    r = _load().orc_vcl_lists(ncl, perm, cls, x, y, z, L, rl, int(bool(half)), cap, nbr, nn)
+    if r != 0:
+        raise ValueError("cluster lists failed")
+    return perm, cls, [nbr[I, :nn[I]].copy() for I in range(ncl)]
 
 
 def forces_cells(pos, L, rc, eps=1.0, sigma=1.0):

@@ -36,6 +36,8 @@
  *      is stable (ties keep ascending original index).
  *   R4 Verlet-list order: the 9 (dz,dy) rows in lexicographic order, inside a
  *      row ascending sorted index; half lists keep only j > i (sorted index).
+ *   R5 Verlet cluster lists: towers, cluster order, boxes and the cluster
+ *      neighbour rule, stated at orc_vcl_order below.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused.
  */
@@ -357,6 +359,131 @@ int orc_verlet(int64_t n, const uint32_t* x, const uint32_t* y, const uint32_t* 
           if (cnt > cap) over = 1;
         }
       }
+  return over;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Verlet cluster lists (Sec. 2.1.1: clusters of a fixed number of nearby    */
+/* particles, with neighbour lists of whole clusters rebuilt every few steps; */
+/* Sec. 5.1: cluster sizes 4, 6 and 8).  Reading R5:                         */
+/*   - towers: n_t x n_t columns over (x, y), n_t the largest k >= 1 with    */
+/*     k^3 M <= n (so a tower cell holds about M particles and a cluster is  */
+/*     about as tall as it is wide); column of a particle                    */
+/*     (cell_coord(x, n_t), cell_coord(y, n_t)), column id cx n_t + cy;      */
+/*   - storage order: by column id, then z, then original index;             */
+/*   - clusters: consecutive runs of M particles of one column, the last run */
+/*     of a column shorter when its count is not a multiple of M;            */
+/*   - a cluster's box is the min/max of its particles' fixed-point          */
+/*     coordinates per axis (a column never wraps in x or y, and z is sorted */
+/*     ascending inside it, so no box wraps);                                */
+/*   - clusters I and J are neighbours iff D^2 <= floor((r_l/u)^2), where    */
+/*     D^2 = sum over axes of d_a^2 and d_a is the periodic distance of the  */
+/*     two boxes' intervals on the 2^32 circle (0 when they intersect);      */
+/*     full lists hold every such J (I itself included), half lists those    */
+/*     with J >= I.  No pair within r_l is missed: |mimg_a(x_i - x_j)| >= d_a */
+/*     for every i in I and j in J.                                          */
+/* ------------------------------------------------------------------------ */
+
+int orc_vcl_ntower(int64_t n, int M) {
+  if (M < 1 || n < 1) return 1;
+  int64_t k = 1;
+  while ((k + 1) * (k + 1) * (k + 1) * (int64_t)M <= n) ++k;
+  return (int)k;
+}
+
+static const uint32_t *g_sx, *g_sy, *g_sz;
+static int g_nt;
+static int cmp_tower_order(const void* a, const void* b) {
+  const uint32_t i = *(const uint32_t*)a, j = *(const uint32_t*)b;
+  const uint64_t ci = (uint64_t)cell_coord(g_sx[i], g_nt) * (uint64_t)g_nt + cell_coord(g_sy[i], g_nt);
+  const uint64_t cj = (uint64_t)cell_coord(g_sx[j], g_nt) * (uint64_t)g_nt + cell_coord(g_sy[j], g_nt);
+  if (ci != cj) return ci < cj ? -1 : 1;
+  if (g_sz[i] != g_sz[j]) return g_sz[i] < g_sz[j] ? -1 : 1;
+  return i < j ? -1 : (i > j ? 1 : 0);
+}
+
+/* perm[k] = original index of the k-th particle in cluster order; cl_start
+ * (capacity n + 1) receives the cluster boundaries.  Returns the number of
+ * clusters, or -1 on bad arguments.  Not thread-safe (qsort comparator state). */
+int64_t orc_vcl_order(int64_t n, const uint32_t* x, const uint32_t* y, const uint32_t* z, int M,
+                      uint32_t* perm, uint32_t* cl_start) {
+  if (n < 1 || M < 1) return -1;
+  const int nt = orc_vcl_ntower(n, M);
+  for (int64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
+  g_sx = x;
+  g_sy = y;
+  g_sz = z;
+  g_nt = nt;
+  qsort(perm, (size_t)n, sizeof(uint32_t), cmp_tower_order);
+  int64_t ncl = 0, k = 0;
+  while (k < n) {
+    /* one column: [k, e) */
+    const uint32_t p = perm[k];
+    const uint32_t cx = cell_coord(x[p], nt), cy = cell_coord(y[p], nt);
+    int64_t e = k;
+    while (e < n && cell_coord(x[perm[e]], nt) == cx && cell_coord(y[perm[e]], nt) == cy) ++e;
+    for (int64_t b = k; b < e; b += M) cl_start[ncl++] = (uint32_t)b;
+    k = e;
+  }
+  cl_start[ncl] = (uint32_t)n;
+  return ncl;
+}
+
+/* periodic distance of the intervals [a0, a1] and [b0, b1] (no wrap inside
+ * either) on the circle of 2^32 fixed-point units */
+static inline uint64_t interval_gap(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
+  if (a0 <= b1 && b0 <= a1) return 0;
+  const uint32_t g1 = b0 - a1, g2 = a0 - b1; /* forward and backward gaps, mod 2^32 */
+  return g1 < g2 ? g1 : g2;
+}
+
+/* Cluster-pair lists by brute force over all cluster pairs (reading R5).
+ * perm / cl_start as from orc_vcl_order; x, y, z in original order.  nbr is
+ * row-major [ncl][cap] of cluster indices in ascending order, nn[ncl] the
+ * complete list lengths (entries beyond cap are dropped).  Returns 0, 1 if a
+ * list exceeded cap, -1 on bad arguments. */
+int orc_vcl_lists(int64_t ncl, const uint32_t* perm, const uint32_t* cl_start, const uint32_t* x,
+                  const uint32_t* y, const uint32_t* z, double L, double rl, int half, int cap, int32_t* nbr,
+                  int32_t* nn) {
+  if (ncl < 0) return -1;
+  const uint64_t R2max = orc_cut2_int(L, rl);
+  uint32_t* bb = (uint32_t*)malloc(sizeof(uint32_t) * 6 * (size_t)(ncl > 0 ? ncl : 1));
+  if (!bb) return -1;
+  for (int64_t c = 0; c < ncl; ++c) {
+    uint32_t* b = bb + 6 * c;
+    const uint32_t p0 = perm[cl_start[c]];
+    b[0] = b[1] = x[p0];
+    b[2] = b[3] = y[p0];
+    b[4] = b[5] = z[p0];
+    for (uint32_t k = cl_start[c] + 1; k < cl_start[c + 1]; ++k) {
+      const uint32_t p = perm[k];
+      if (x[p] < b[0]) b[0] = x[p];
+      if (x[p] > b[1]) b[1] = x[p];
+      if (y[p] < b[2]) b[2] = y[p];
+      if (y[p] > b[3]) b[3] = y[p];
+      if (z[p] < b[4]) b[4] = z[p];
+      if (z[p] > b[5]) b[5] = z[p];
+    }
+  }
+  int over = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : over)
+  for (int64_t I = 0; I < ncl; ++I) {
+    const uint32_t* a = bb + 6 * I;
+    int cnt = 0;
+    for (int64_t J = half ? I : 0; J < ncl; ++J) {
+      const uint32_t* b = bb + 6 * J;
+      const uint64_t dx = interval_gap(a[0], a[1], b[0], b[1]);
+      const uint64_t dy = interval_gap(a[2], a[3], b[2], b[3]);
+      const uint64_t dz = interval_gap(a[4], a[5], b[4], b[5]);
+      const uint64_t D2 = dx * dx + dy * dy + dz * dz;
+      if (D2 > R2max) continue;
+      if (cnt < cap) nbr[I * cap + cnt] = (int32_t)J;
+      ++cnt;
+    }
+    nn[I] = cnt;
+    if (cnt > cap) over = 1;
+  }
+  free(bb);
   return over;
 }
 

@@ -285,6 +285,112 @@ def test_bin_cells_is_stable_counting_sort(orc):
         assert orc.cell_of((xv, 0, 0), nc) == (xv * nc) // TWO32
 
 
+# --- Verlet cluster lists (Sec. 2.1.1; cluster sizes of Sec. 5.1; reading R5) ---
+
+@pytest.mark.parametrize("n,M,k", [(1, 4, 1), (3, 4, 1), (1000, 4, 6), (1048576, 4, 64), (1048576, 8, 50),
+                                   (1048576, 6, 55), (2000000, 8, 62)])
+def test_vcl_tower_count(orc, n, M, k):
+    assert orc.vcl_ntower(n, M) == k
+    assert k ** 3 * M <= n or k == 1
+    assert (k + 1) ** 3 * M > n
+
+
+def vcl_cases():
+    rng = np.random.default_rng(7)
+    out = [(name, L, pos) for name, L, pos in tiny_cases()]
+    s = W.stratified(3000, 0.75, 11)
+    out.append(("fluid", s.L, s.pos))
+    s = W.slab(2500, 0.8, 0.02, 0.4, 12)
+    out.append(("slab", s.L, s.pos))
+    out.append(("dup_z", 6.0, np.vstack([rng.integers(0, TWO32, size=(2, 200), dtype=np.uint64),
+                                         np.repeat(rng.integers(0, TWO32, size=(1, 20), dtype=np.uint64), 10, axis=1)]
+                                        ).astype(np.uint32)))
+    return out
+
+
+@pytest.mark.parametrize("M", [1, 4, 6, 8])
+def test_vcl_order_is_tower_z_sort(orc, M):
+    for name, L, pos in vcl_cases():
+        n = pos.shape[1]
+        perm, cls = orc.vcl_order(pos, M)
+        nt = orc.vcl_ntower(n, M)
+        assert np.array_equal(np.sort(perm), np.arange(n)), name
+        col = (pos[0].astype(np.int64) * nt >> 32) * nt + (pos[1].astype(np.int64) * nt >> 32)
+        # a lexicographic sort by (column, z, original index), written with numpy
+        assert np.array_equal(perm, np.lexsort((np.arange(n), pos[2], col))), name
+        sizes = np.diff(cls)
+        assert cls[0] == 0 and cls[-1] == n and sizes.min() >= 1 and sizes.max() <= M, name
+        ccol = col[perm]
+        for c in range(len(sizes)):
+            members = ccol[cls[c]:cls[c + 1]]
+            assert (members == members[0]).all(), name               # one tower per cluster
+            last_of_tower = cls[c + 1] == n or ccol[cls[c + 1]] != members[0]
+            assert sizes[c] == M or last_of_tower, name               # only a tower's last cluster is short
+            if cls[c] > 0 and ccol[cls[c] - 1] == members[0]:
+                assert sizes[c - 1] == M, name
+
+
+def _clusters_of(perm, cls, n):
+    cl = np.empty(n, dtype=np.int64)
+    for c in range(len(cls) - 1):
+        cl[perm[cls[c]:cls[c + 1]]] = c
+    return cl
+
+
+def test_vcl_lists_with_singleton_clusters_are_verlet_lists(orc):
+    """M = 1: every box is a point and D^2 is the pair's R^2, so the cluster
+    lists are the particle Verlet lists (plus the particle itself)."""
+    for name, L, pos in vcl_cases()[:6]:
+        n, rl = pos.shape[1], 1.0
+        perm, cls, lists = orc.vcl_lists(pos, L, rl, 1, 0)
+        cl = _clusters_of(perm, cls, n)
+        want = [set() for _ in range(n)]
+        for i in range(n):
+            want[cl[i]].add(int(cl[i]))
+        for i, j in orc.pairs_bruteforce(pos, L, rl):
+            want[cl[i]].add(int(cl[j]))
+            want[cl[j]].add(int(cl[i]))
+        zero = [(i, j) for i in range(n) for j in range(i + 1, n) if orc.r2_int(pos[:, i], pos[:, j]) == 0]
+        for i, j in zero:
+            want[cl[i]].add(int(cl[j]))
+            want[cl[j]].add(int(cl[i]))
+        got = [set(int(v) for v in lists[c]) for c in range(n)]
+        assert got == [want[c] for c in range(n)], name
+
+
+@pytest.mark.parametrize("M", [4, 6, 8])
+def test_vcl_lists_cover_every_pair_and_stay_near(orc, M):
+    """Every pair within r_l lands in a listed cluster pair; every listed pair
+    has two members within r_l plus both boxes' diagonals; full lists are
+    symmetric and half lists are the full ones with J >= I."""
+    for name, L, pos in vcl_cases():
+        n = pos.shape[1]
+        rl = 1.0 if L < 7 else 2.8
+        perm, cls, full = orc.vcl_lists(pos, L, rl, M, 0)
+        _, _, half = orc.vcl_lists(pos, L, rl, M, 1)
+        ncl = len(cls) - 1
+        cl = _clusters_of(perm, cls, n)
+        fs = [set(int(v) for v in full[c]) for c in range(ncl)]
+        for I in range(ncl):
+            assert list(full[I]) == sorted(fs[I]) and I in fs[I], name
+            assert set(int(v) for v in half[I]) == {J for J in fs[I] if J >= I}, name
+            for J in fs[I]:
+                assert I in fs[J], name
+        for i, j in orc.pairs_bruteforce(pos, L, rl):
+            assert int(cl[j]) in fs[cl[i]], name
+        u = L / TWO32
+        lo = np.array([pos[:, perm[cls[c]:cls[c + 1]]].min(axis=1) for c in range(ncl)], dtype=np.float64)
+        hi = np.array([pos[:, perm[cls[c]:cls[c + 1]]].max(axis=1) for c in range(ncl)], dtype=np.float64)
+        diag = np.sqrt(((hi - lo) ** 2).sum(axis=1)) * u
+        rng = np.random.default_rng(5)
+        for I in rng.choice(ncl, size=min(ncl, 40), replace=False):
+            mi = perm[cls[I]:cls[I + 1]]
+            for J in fs[I]:
+                mj = perm[cls[J]:cls[J + 1]]
+                d = min(math.sqrt(orc.r2_int(pos[:, a], pos[:, b])) * u for a in mi for b in mj)
+                assert d <= rl + diag[I] + diag[J] + 1e-9, name
+
+
 # --- integrator ----------------------------------------------------------------
 
 def test_velocity_verlet_two_body_harmonic_period(orc):
