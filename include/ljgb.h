@@ -62,8 +62,12 @@ typedef enum {
 typedef enum { LJ_PREC_FP64 = 0, LJ_PREC_FP32_ACC64 = 1 } lj_precision;
 
 /* Neighbour identification (Sec. 2.1.1): linked cells of edge >= r_c, rebinned
- * at every force evaluation; Verlet lists built on cells of edge >= r_c + skin. */
-typedef enum { LJ_LC = 0, LJ_VL = 1 } lj_container;
+ * at every force evaluation; Verlet lists built on cells of edge >= r_c + skin;
+ * Verlet cluster lists: clusters of M particles (M = 4, 6 or 8, the cluster
+ * sizes of Sec. 5.1) with lists of whole neighbour clusters within r_c + skin
+ * (see lj_build_clusters).  Both list containers are rebuilt every few steps
+ * and whenever a particle has moved more than skin/2 since the build. */
+typedef enum { LJ_LC = 0, LJ_VL = 1, LJ_VCL = 2 } lj_container;
 
 /* Interaction orders: the GPU analogues of the paper's register-filling
  * patterns (Sec. 4.1.1, Fig. 4).
@@ -77,14 +81,21 @@ typedef enum { LJ_LC = 0, LJ_VL = 1 } lj_container;
  *                    w=32, 2/V2 for w=16, V2/2 for w=2.
  *   LJ_ORD_ROT32     one i and one j per lane, j rotated through the warp by
  *                    shuffles: a full 32 x 32 tile (the "full/rotated" order).
- *   LJ_ORD_VL_IPT    Verlet lists only: one i per lane, gathering its list. */
+ *   LJ_ORD_VL_IPT    Verlet lists only: one i per lane, gathering its list.
+ *   LJ_ORD_CL_TILE   cluster lists only (param = cluster size M): lane =
+ *                    (i of the base cluster, j-slot), 32/M j's per pass from
+ *                    one or more neighbour clusters.
+ *   LJ_ORD_CL_JLANE  cluster lists only (param = M): one j per lane (32 per
+ *                    pass), the M base-cluster i's held in every lane. */
 typedef enum {
   LJ_ORD_IPT_SMEM = 0,
   LJ_ORD_IPT_TMA = 1,
   LJ_ORD_KI = 2,
   LJ_ORD_JSPLIT = 3,
   LJ_ORD_ROT32 = 4,
-  LJ_ORD_VL_IPT = 5
+  LJ_ORD_VL_IPT = 5,
+  LJ_ORD_CL_TILE = 6,
+  LJ_ORD_CL_JLANE = 7
 } lj_order;
 
 /* Newton's third law (Sec. 2.1, Sec. 4.1.3): off (every pair evaluated from
@@ -149,9 +160,38 @@ lj_status lj_bin_cells(lj_ctx* ctx, int32_t container);
  * Bins first.  Grows the list capacity and rebuilds on overflow. */
 lj_status lj_build_verlet(lj_ctx* ctx, int32_t half_list);
 
+/* Build Verlet cluster lists (Sec. 2.1.1, the cluster container; cluster size
+ * M in {4, 6, 8}, Sec. 5.1).  The particle storage is reordered into cluster
+ * order: n_t x n_t towers over (x, y), n_t the largest k >= 1 with
+ * k^3 M <= n; tower of a particle (floor(x_fp n_t / 2^32), floor(y_fp n_t /
+ * 2^32)); storage by tower id cx n_t + cy, then z_fp, then original index.
+ * Each tower's run is cut into clusters of M consecutive particles (the last
+ * one shorter).  A cluster's box is the min/max of its fixed-point
+ * coordinates; clusters I and J are neighbours iff the sum over the axes of
+ * the squared periodic distances between their boxes' intervals is at most
+ * floor(((r_c + skin)/u)^2), decided in 64-bit integers.  Full lists hold
+ * every neighbour J (I itself included); half lists (half_list = 1, for
+ * Newton-3) only J >= I.  Grows the list capacity and rebuilds on overflow.
+ * Errors: LJ_ERR_ARG (M not 4, 6 or 8; n >= 2^29), LJ_ERR_STATE,
+ * LJ_ERR_CAPACITY, LJ_ERR_OOM, LJ_ERR_CUDA. */
+lj_status lj_build_clusters(lj_ctx* ctx, int32_t M, int32_t half_list);
+
+/* The current cluster order (after lj_build_clusters or a force evaluation on
+ * LJ_VCL): *ncl receives the number of clusters, cl_start (ncl + 1 entries,
+ * host, may be NULL) the first storage slot of each cluster and n at the end
+ * (lj_get_cells gives perm), *ntower (may be NULL) n_t.  Errors: LJ_ERR_STATE
+ * if no cluster order is current. */
+lj_status lj_get_clusters(lj_ctx* ctx, int64_t* ncl, uint32_t* cl_start, int32_t* ntower);
+
+/* The cluster-pair lists: nn[ncl] their lengths and nbr[ncl][cap] (row-major,
+ * host) the neighbour cluster indices in the library's search order (the set
+ * is defined; the order is not); *cap_out the capacity.  Either array may be
+ * NULL.  Errors: LJ_ERR_STATE if no cluster list is current. */
+lj_status lj_get_cluster_lists(lj_ctx* ctx, int32_t* nbr, int32_t* nn, int32_t* cap_out);
+
 /* One force evaluation F_i = sum_j F_ij (Eq. 1) with the given configuration.
- * LC rebins; VL builds the list when it is stale (never built, other half
- * mode, or a particle moved more than skin/2).  energy_out / virial_out (host,
+ * LC rebins; VL and VCL build their lists when they are stale (never built,
+ * other half mode or cluster size, or a particle moved more than skin/2).  energy_out / virial_out (host,
  * may be NULL) receive U = sum_pairs U(r) and W = sum_pairs r . F_ij.
  * Forces stay on the device (lj_get_forces).  Errors: LJ_ERR_ARG (invalid
  * configuration; see lj_config_valid), LJ_ERR_STATE, LJ_ERR_NONFINITE, LJ_ERR_CUDA. */

@@ -95,6 +95,11 @@ bool order_is_valid(const lj_config& g) {
     }
     return g.newton3 == LJ_N3_OFF || g.newton3 == LJ_N3_ATOMIC || g.newton3 == LJ_N3_ATOMIC_BWD;
   }
+  if (g.container == LJ_VCL) {
+    if (g.order != LJ_ORD_CL_TILE && g.order != LJ_ORD_CL_JLANE) return false;
+    if (g.param != 4 && g.param != 6 && g.param != 8) return false;
+    return g.newton3 == LJ_N3_OFF || g.newton3 == LJ_N3_ATOMIC;
+  }
   if (g.container == LJ_VL) {
     if (g.order == LJ_ORD_VL_IPT) return g.param == 0 && g.newton3 >= LJ_N3_OFF && g.newton3 <= LJ_N3_TWOPASS;
     if (g.order == LJ_ORD_JSPLIT) {
@@ -128,6 +133,10 @@ std::vector<lj_config> all_configs() {
   v.push_back({LJ_LC, LJ_ORD_KI, 4, LJ_N3_ATOMIC_BWD});
   for (int w : {32, 16, 8, 4, 2}) v.push_back({LJ_LC, LJ_ORD_JSPLIT, w, LJ_N3_ATOMIC_BWD});
   v.push_back({LJ_LC, LJ_ORD_ROT32, 0, LJ_N3_ATOMIC_BWD});
+  // cluster lists: order x cluster size x Newton-3
+  for (int n3 : n3s)
+    for (int ord : {LJ_ORD_CL_TILE, LJ_ORD_CL_JLANE})
+      for (int m : {4, 6, 8}) v.push_back({LJ_VCL, ord, m, n3});
   return v;
 }
 
@@ -184,6 +193,9 @@ void reset_state_flags(Ctx& c) {
   c.vl_valid = false;
   c.rev_valid = false;
   c.vl_half = -1;
+  c.vcl_valid = false;
+  c.vcl_half = -1;
+  c.vcl_M = 0;
   c.forces_valid = false;
   c.tiles_gen = ~0ull;
   c.moved = true;
@@ -281,9 +293,99 @@ lj_status do_build_verlet(Ctx& c, int half, int colmajor, bool twopass) {
   return LJ_OK;
 }
 
+// Cluster order and cluster-pair lists for cluster size M (regrowing on
+// overflow); the cluster order's binning snapshots the positions for the
+// skin/2 rule.
+lj_status do_build_vcl(Ctx& c, int M, int half) {
+  c.skin_pending = false;
+  if (c.n >= (int64_t(1) << 29)) return fail(c, LJ_ERR_ARG, "cluster lists hold at most 2^29 - 1 particles");
+  int64_t ncl = 0;
+  CK(vcl_bin(c, M, &ncl));
+  c.launches += 13;  // tower ids, 3 scan passes, keys, per-cell sort, permute, cluster count + 3 scan passes, ...
+  c.binned_for = LJ_VCL;
+  c.vl_valid = false;
+  c.rev_valid = false;
+  c.moved = false;
+  if (c.vcl_cap == 0) {
+    // neighbour clusters: the boxes' Minkowski sum with the r_l ball, about
+    // (a + 2 r_l)^3 for a cluster edge a = (M / rho)^(1/3), over M per cluster
+    const double rho = (double)c.n / (c.L * c.L * c.L), rl = c.rc + c.skin;
+    const double a = std::cbrt((double)M / rho);
+    const double m = std::pow(a + 2.0 * rl, 3.0) * rho / M * (half ? 0.6 : 1.2) + 16.0;
+    c.vcl_cap = (int)std::min<double>(std::ceil(m / 8.0) * 8.0, (double)std::max<int64_t>(ncl, 8) + 8.0);
+  }
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (c.vcl_nbr_cap < (size_t)c.vcl_cap * ncl || !c.vcl_nbr) {
+      dfree(c.vcl_nbr);
+      c.vcl_nbr = nullptr;
+      c.vcl_nbr_cap = 0;
+      CK(cudaMalloc(&c.vcl_nbr, (size_t)c.vcl_cap * ncl * sizeof(uint32_t)));
+      c.vcl_nbr_cap = (size_t)c.vcl_cap * ncl;
+    }
+    if (c.vcl_nn_cap < (size_t)ncl || !c.vcl_nn) {
+      dfree(c.vcl_nn);
+      c.vcl_nn = nullptr;
+      CK(dalloc(c.vcl_nn, (size_t)ncl));
+      c.vcl_nn_cap = (size_t)ncl;
+    }
+    CK(cudaMemsetAsync(c.maxlen, 0, sizeof(uint32_t), c.stream));
+    CK(launch_vcl_build(c, half, c.maxlen));
+    c.launches += 1;
+    uint32_t ml = 0;
+    CK(cudaMemcpyAsync(c.host_status, c.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(&ml, c.maxlen, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (!(*c.host_status & ST_CAPACITY)) break;
+    CK(cudaMemsetAsync(c.status, 0, sizeof(uint32_t), c.stream));
+    c.vcl_cap = (int)((ml + 15) / 8) * 8;
+    c.counters[4] += 1;
+    if (attempt == 3) return fail(c, LJ_ERR_CAPACITY, "cluster list capacity could not be grown");
+  }
+  if (*c.host_status & ST_SKIN) {  // a fresh list makes an earlier skin flag stale
+    *c.host_status &= ~ST_SKIN;
+    CK(cudaMemcpyAsync(c.status, c.host_status, sizeof(uint32_t), cudaMemcpyHostToDevice, c.stream));
+  }
+  c.vcl_half = half;
+  c.vcl_valid = true;
+  c.steps_since_build = 0;
+  c.counters[2] += 1;
+  return LJ_OK;
+}
+
+// Lists of either list container exist for the current storage order (their
+// build snapshot is what the skin/2 rule compares against).
+bool lists_current(const Ctx& c) {
+  return (c.vl_valid && c.binned_for == LJ_VL) || (c.vcl_valid && c.binned_for == LJ_VCL);
+}
+
+// The current lists are the ones cfg evaluates on.
+bool lists_match(const Ctx& c, const lj_config& cfg) {
+  const int half = cfg.newton3 != LJ_N3_OFF ? 1 : 0;
+  if (cfg.container == LJ_VL)
+    return c.vl_valid && c.binned_for == LJ_VL && c.vl_half == half &&
+           c.vl_colmajor == (cfg.order == LJ_ORD_VL_IPT ? 1 : 0) && (cfg.newton3 != LJ_N3_TWOPASS || c.rev_valid);
+  if (cfg.container == LJ_VCL)
+    return c.vcl_valid && c.binned_for == LJ_VCL && c.vcl_half == half && c.vcl_M == cfg.param;
+  return false;
+}
+
+// (Re)builds the lists of a list container for cfg.
+lj_status build_lists(Ctx& c, const lj_config& cfg) {
+  const int half = cfg.newton3 != LJ_N3_OFF ? 1 : 0;
+  if (cfg.container == LJ_VCL) {
+    CKS(do_build_vcl(c, cfg.param, half));
+    c.P.nc = c.vcl_nt;
+  } else {
+    CKS(do_build_verlet(c, half, cfg.order == LJ_ORD_VL_IPT ? 1 : 0, cfg.newton3 == LJ_N3_TWOPASS));
+    c.P.nc = c.nc_vl;
+  }
+  c.moved_since_build = false;
+  return LJ_OK;
+}
+
 // Displacement check since the last build (skin/2 rule), synchronous.
 lj_status list_is_fresh(Ctx& c, bool& fresh) {
-  fresh = c.vl_valid && c.binned_for == LJ_VL;
+  fresh = lists_current(c);
   if (!fresh || !c.moved_since_build) return LJ_OK;
   CK(launch_kick_drift(c, 0.0, 0.0, false, true) == cudaSuccess ? cudaSuccess : cudaErrorUnknown);
   uint32_t st = 0;
@@ -305,26 +407,21 @@ lj_status prepare(Ctx& c, const lj_config& cfg, bool allow_rebuild_schedule) {
     c.P.nc = c.nc_lc;
     return LJ_OK;
   }
-  const int half = cfg.newton3 != LJ_N3_OFF ? 1 : 0;
-  const int colmajor = cfg.order == LJ_ORD_VL_IPT ? 1 : 0;
-  const bool twopass = cfg.newton3 == LJ_N3_TWOPASS;
   bool fresh = false;
   CKS(list_is_fresh(c, fresh));
-  if (fresh && c.vl_half == half && c.vl_colmajor == colmajor && (!twopass || c.rev_valid)) {
-    c.P.nc = c.nc_vl;
+  if (fresh && lists_match(c, cfg)) {
+    c.P.nc = cfg.container == LJ_VCL ? c.vcl_nt : c.nc_vl;
     return LJ_OK;
   }
-  if (c.vl_valid && c.moved_since_build) c.counters[3] += 1;
-  CKS(do_build_verlet(c, half, colmajor, twopass));
-  c.moved_since_build = false;
-  c.P.nc = c.nc_vl;
-  return LJ_OK;
+  if (lists_current(c) && c.moved_since_build) c.counters[3] += 1;
+  return build_lists(c, cfg);
 }
 
 // Kernels launched by the force dispatch (pair kernel + tile build when
 // needed, or pair kernel + gather for the two-pass variant).
 int force_launches(const Ctx& c, const lj_config& cfg, bool tiles_rebuilt) {
   if (cfg.container == LJ_VL) return cfg.newton3 == LJ_N3_TWOPASS ? 2 : 1;
+  if (cfg.container == LJ_VCL) return 1;
   if (cfg.order == LJ_ORD_JSPLIT) return 1;
   return 1 + (tiles_rebuilt ? 5 : 0);
 }
@@ -368,6 +465,8 @@ lj_status run_force(Ctx& c, const lj_config& cfg, bool ev, bool acc_zeroed = fal
   if (t0) CK(cudaEventRecord(t0, c.stream));
   if (cfg.container == LJ_LC)
     e = f64 ? force_lc_f64(c, cfg, ev) : force_lc_f32(c, cfg, ev);
+  else if (cfg.container == LJ_VCL)
+    e = f64 ? force_vcl_f64(c, cfg, ev) : force_vcl_f32(c, cfg, ev);
   else
     e = f64 ? force_vl_f64(c, cfg, ev) : force_vl_f32(c, cfg, ev);
   if (t1) CK(cudaEventRecord(t1, c.stream));
@@ -386,23 +485,18 @@ lj_status force_eval(Ctx& c, const lj_config& cfg, double* energy, double* viria
   if (!order_is_valid(cfg)) return fail(c, LJ_ERR_ARG, "invalid configuration");
   CKS(need_particles(c));
   const bool ev = energy || virial;
-  const bool twopass = cfg.newton3 == LJ_N3_TWOPASS;
-  if (c.skin_pending && cfg.container == LJ_VL && c.vl_valid && c.binned_for == LJ_VL &&
-      c.vl_half == (cfg.newton3 != LJ_N3_OFF ? 1 : 0) && c.vl_colmajor == (cfg.order == LJ_ORD_VL_IPT ? 1 : 0) &&
-      (!twopass || c.rev_valid)) {
+  if (c.skin_pending && lists_match(c, cfg)) {
     // positions came from lj_update_positions, whose kernel checked the skin:
     // evaluate on the current lists at once and read the flag meanwhile; if a
     // particle left its skin, rebuild and evaluate again
     c.skin_pending = false;
-    c.P.nc = c.nc_vl;
+    c.P.nc = cfg.container == LJ_VCL ? c.vcl_nt : c.nc_vl;
     CKS(run_force(c, cfg, ev));
     CK(cudaEventSynchronize(c.drift_done));
     if (*reinterpret_cast<volatile uint32_t*>(c.skin_host)) {
       c.counters[3] += 1;
       CK(cudaMemsetAsync(c.status, 0, sizeof(uint32_t), c.stream));  // the speculative run's status is void
-      CKS(do_build_verlet(c, cfg.newton3 != LJ_N3_OFF ? 1 : 0, cfg.order == LJ_ORD_VL_IPT ? 1 : 0, twopass));
-      c.moved_since_build = false;
-      c.P.nc = c.nc_vl;
+      CKS(build_lists(c, cfg));
       CKS(run_force(c, cfg, ev));
     }
   } else {
@@ -596,7 +690,7 @@ lj_status lj_update_positions(lj_ctx* h, const double* pos, int32_t on_device) {
     dpos = (const double*)c.stage;
   }
   // with current lists the update kernel also checks the skin (mapped flag)
-  const bool check = c.vl_valid && c.binned_for == LJ_VL;
+  const bool check = lists_current(c);
   const double hs = 0.5 * c.skin * 4294967296.0 / c.L;
   const uint64_t d2max = hs * hs >= 1.8e19 ? ~0ull : (uint64_t)(hs * hs);
   if (check) *reinterpret_cast<volatile uint32_t*>(c.skin_host) = 0u;
@@ -631,6 +725,60 @@ lj_status lj_build_verlet(lj_ctx* h, int32_t half_list) {
   return LJ_OK;
 }
 
+lj_status lj_build_clusters(lj_ctx* h, int32_t M, int32_t half_list) {
+  if (!h) return LJ_ERR_ARG;
+  Ctx& c = h->c;
+  CKS(need_particles(c));
+  if (M != 4 && M != 6 && M != 8) return fail(c, LJ_ERR_ARG, "cluster size must be 4, 6 or 8");
+  CKS(settle_kick(c));
+  CKS(do_build_vcl(c, M, half_list ? 1 : 0));
+  c.moved_since_build = false;
+  return LJ_OK;
+}
+
+lj_status lj_get_clusters(lj_ctx* h, int64_t* ncl, uint32_t* cl_start, int32_t* ntower) {
+  if (!h || !ncl) return LJ_ERR_ARG;
+  Ctx& c = h->c;
+  if (c.binned_for != LJ_VCL || c.vcl_M == 0) return fail(c, LJ_ERR_STATE, "no cluster order is current");
+  *ncl = c.vcl_ncl;
+  if (ntower) *ntower = c.vcl_nt;
+  if (cl_start) {
+    CK(cudaMemcpyAsync(cl_start, c.cl_start, ((size_t)c.vcl_ncl + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                       c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+  }
+  return LJ_OK;
+}
+
+lj_status lj_get_cluster_lists(lj_ctx* h, int32_t* nbr, int32_t* nn, int32_t* cap_out) {
+  if (!h) return LJ_ERR_ARG;
+  Ctx& c = h->c;
+  if (!c.vcl_valid || c.binned_for != LJ_VCL) return fail(c, LJ_ERR_STATE, "no cluster list built");
+  const size_t ncl = (size_t)c.vcl_ncl, cap = (size_t)c.vcl_cap;
+  if (cap_out) *cap_out = c.vcl_cap;
+  if (nn) CK(cudaMemcpyAsync(nn, c.vcl_nn, ncl * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  if (nbr) {
+    // packed entries (first slot << 3 | size - 1) back to cluster indices
+    std::vector<uint32_t> packed(ncl * cap), cs(ncl + 1);
+    CK(cudaMemcpyAsync(packed.data(), c.vcl_nbr, ncl * cap * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(cs.data(), c.cl_start, (ncl + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    std::vector<int32_t> len(ncl);
+    CK(cudaMemcpy(len.data(), c.vcl_nn, ncl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (size_t I = 0; I < ncl; ++I)
+      for (size_t k = 0; k < cap; ++k) {
+        if ((int32_t)k >= len[I]) {
+          nbr[I * cap + k] = -1;
+          continue;
+        }
+        const uint32_t b = packed[I * cap + k] >> 3;
+        nbr[I * cap + k] = (int32_t)(std::lower_bound(cs.begin(), cs.end() - 1, b) - cs.begin());
+      }
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  return LJ_OK;
+}
+
 int32_t lj_config_valid(lj_config cfg) { return order_is_valid(cfg) ? 1 : 0; }
 
 int32_t lj_config_list(lj_config* out, int32_t cap) {
@@ -653,7 +801,7 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
   if (!(dt > 0) || nsteps < 0 || rebuild_every < 1) return fail(c, LJ_ERR_ARG, "need dt > 0, nsteps >= 0, rebuild_every >= 1");
   const double hdtm = 0.5 * dt / c.mass;
   const double dtu = dt * 4294967296.0 / c.L;
-  const bool vl = cfg.container == LJ_VL;
+  const bool vl = cfg.container != LJ_LC;  // a list container
   c.skin_pending = false;  // the steps below check the skin themselves
   if (!c.forces_valid || memcmp(&c.last_cfg, &cfg, sizeof(cfg)) != 0) {
     CKS(prepare(c, cfg, false));
@@ -664,7 +812,7 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
   // step's first kick (the next call's, or lj_get_state / lj_kinetic_energy /
   // a force evaluation apply it on their own): one kernel per step less.
   for (int s = 0; s < nsteps; ++s) {
-    const bool track = vl && c.vl_valid;
+    const bool track = vl && lists_match(c, cfg);
     const bool speculate = track && c.steps_since_build + 1 < rebuild_every;
     if (speculate) *reinterpret_cast<volatile uint32_t*>(c.skin_host) = 0u;
     CK(launch_kick_drift(c, hdtm, dtu, false, track, speculate ? c.skin_dev : nullptr,
@@ -675,7 +823,7 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
     c.moved_since_build = true;
     if (vl) {
       c.steps_since_build += 1;
-      const bool scheduled = c.steps_since_build >= rebuild_every || !c.vl_valid;
+      const bool scheduled = c.steps_since_build >= rebuild_every || !lists_match(c, cfg);
       bool rebuild = scheduled;
       if (!scheduled) {
         // The drift writes its skin flag to mapped host memory and the force
@@ -685,7 +833,7 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
         // forces computed again, replacing the speculative ones (and any
         // status they raised).
         CK(cudaEventRecord(c.drift_done, c.stream));
-        c.P.nc = c.nc_vl;
+        c.P.nc = cfg.container == LJ_VCL ? c.vcl_nt : c.nc_vl;
         CKS(run_force(c, cfg, false, true));
         CK(cudaEventSynchronize(c.drift_done));
         if (*reinterpret_cast<volatile uint32_t*>(c.skin_host)) {
@@ -695,10 +843,7 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
         }
       }
       if (rebuild) {
-        CKS(do_build_verlet(c, cfg.newton3 != LJ_N3_OFF ? 1 : 0, cfg.order == LJ_ORD_VL_IPT ? 1 : 0,
-                            cfg.newton3 == LJ_N3_TWOPASS));
-        c.moved_since_build = false;
-        c.P.nc = c.nc_vl;
+        CKS(build_lists(c, cfg));
         CKS(run_force(c, cfg, false));
       }
     } else {
@@ -916,6 +1061,7 @@ lj_status lj_features(lj_ctx* h, double* out) {
   c.binned_nc = 0;
   c.moved = true;
   c.vl_valid = false;
+  c.vcl_valid = false;
   const double n = (double)c.n, L = c.L;
   const double ncell = (double)c.nc_lc * c.nc_lc * c.nc_lc;
   const double s1 = (double)st[0], s2 = (double)st[1];
@@ -949,7 +1095,8 @@ void lj_destroy(lj_ctx* h) {
   void* dev[] = {c.pos, c.inv, c.pos_alt, c.vel, c.vel_alt, c.frc, c.frc_alt, c.cell_start, c.cnt, c.cell_of, c.slot,
                  c.key, c.scan_tmp, c.tiles, c.row_tiles, c.nbr, c.nnbr, c.x_build, c.maxlen, c.twopass,
                  c.rev_cnt, c.rev_start, c.rev_slot, c.rev_key, c.rev_key2, c.ev, c.status,
-                 c.feat_stats, c.tile_ctr, c.stage, c.nbr16};
+                 c.feat_stats, c.tile_ctr, c.stage, c.nbr16, c.tower_cl, c.cl_start, c.cl_lo, c.cl_hi, c.cl_z,
+                 c.vcl_nbr, c.vcl_nn};
   for (void* p : dev) dfree(p);
   if (c.host_ev) cudaFreeHost(c.host_ev);
   if (c.host_np) cudaFreeHost(c.host_np);

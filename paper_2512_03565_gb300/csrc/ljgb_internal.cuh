@@ -363,6 +363,30 @@ struct Ctx {
   uint32_t* maxdisp = nullptr;  // device max |displacement| (units)
   int steps_since_build = 0;
 
+  // Verlet cluster lists (k_vcl.cu): cluster order for cluster size vcl_M,
+  // clusters [cl_start[c], cl_start[c+1]) with boxes cl_lo / cl_hi, and the
+  // row-major cluster-pair lists [ncl][vcl_cap] of packed entries
+  // (begin << 3) | (size - 1)
+  int vcl_M = 0;
+  int vcl_nt = 0;               // towers per axis
+  int64_t vcl_ncl = 0;
+  int vcl_half = -1;
+  bool vcl_valid = false;
+  uint32_t* tower_cl = nullptr; // first cluster of each tower (nt^2 + 1)
+  size_t tower_cl_cap = 0;
+  uint32_t* cl_start = nullptr;
+  size_t cl_start_cap = 0;
+  uint4* cl_lo = nullptr;
+  size_t cl_lo_cap = 0;
+  uint4* cl_hi = nullptr;
+  size_t cl_hi_cap = 0;
+  uint32_t* cl_z = nullptr;     // zmin of every cluster, then zmax
+  size_t cl_z_cap = 0;
+  uint32_t* vcl_nbr = nullptr;
+  int32_t* vcl_nn = nullptr;
+  int vcl_cap = 0;
+  size_t vcl_nbr_cap = 0, vcl_nn_cap = 0;
+
   // two-pass Newton-3: per-entry slots R[3][cap*n] and the reverse index
   void* twopass = nullptr;
   size_t twopass_bytes = 0;
@@ -433,6 +457,11 @@ cudaError_t launch_iota(uint32_t* inv, int64_t n, cudaStream_t s);
 cudaError_t launch_from_slots(const uint32_t* inv, const double* src3, int64_t n, double* dst3, cudaStream_t s);
 cudaError_t launch_reverse_index(Ctx& c);
 cudaError_t launch_list_to16(Ctx& c, uint32_t* overflow);
+int vcl_ntower(int64_t n, int M);
+cudaError_t vcl_bin(Ctx& c, int M, int64_t* ncl_out);
+cudaError_t launch_vcl_build(Ctx& c, int half, uint32_t* maxlen);
+cudaError_t force_vcl_f32(Ctx& c, const lj_config& cfg, bool ev);
+cudaError_t force_vcl_f64(Ctx& c, const lj_config& cfg, bool ev);
 
 // Thresholds for coarse_r2 (units of 2^18 u^2) around the integer threshold
 // R2max: certainly inside below *lo, certainly outside above *hi.  The band

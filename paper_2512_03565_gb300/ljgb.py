@@ -26,10 +26,11 @@ LJ_OK, LJ_ERR_ARG, LJ_ERR_CUDA, LJ_ERR_CAPACITY, LJ_ERR_SKIN, LJ_ERR_NONFINITE, 
 STATUS_NAMES = ["LJ_OK", "LJ_ERR_ARG", "LJ_ERR_CUDA", "LJ_ERR_CAPACITY", "LJ_ERR_SKIN",
                 "LJ_ERR_NONFINITE", "LJ_ERR_TIMEOUT", "LJ_ERR_STATE", "LJ_ERR_OOM"]
 LJ_PREC_FP64, LJ_PREC_FP32_ACC64 = 0, 1
-LJ_LC, LJ_VL = 0, 1
-LJ_ORD_IPT_SMEM, LJ_ORD_IPT_TMA, LJ_ORD_KI, LJ_ORD_JSPLIT, LJ_ORD_ROT32, LJ_ORD_VL_IPT = range(6)
+LJ_LC, LJ_VL, LJ_VCL = 0, 1, 2
+LJ_ORD_IPT_SMEM, LJ_ORD_IPT_TMA, LJ_ORD_KI, LJ_ORD_JSPLIT, LJ_ORD_ROT32, LJ_ORD_VL_IPT, LJ_ORD_CL_TILE, \
+    LJ_ORD_CL_JLANE = range(8)
 LJ_N3_OFF, LJ_N3_ATOMIC, LJ_N3_TWOPASS, LJ_N3_ATOMIC_BWD = 0, 1, 2, 3
-ORDER_NAMES = ["IPT_SMEM", "IPT_TMA", "KI", "JSPLIT", "ROT32", "VL_IPT"]
+ORDER_NAMES = ["IPT_SMEM", "IPT_TMA", "KI", "JSPLIT", "ROT32", "VL_IPT", "CL_TILE", "CL_JLANE"]
 
 
 class lj_config(C.Structure):
@@ -47,7 +48,7 @@ def config(container, order, param=0, newton3=LJ_N3_OFF) -> lj_config:
 
 
 def config_name(c: lj_config) -> str:
-    cont = "LC" if c.container == LJ_LC else "VL"
+    cont = {LJ_LC: "LC", LJ_VL: "VL", LJ_VCL: "VCL"}.get(c.container, f"c{c.container}")
     o = ORDER_NAMES[c.order] if 0 <= c.order < len(ORDER_NAMES) else f"ord{c.order}"
     p = f"-{c.param}" if c.param else ""
     n3 = ["N3off", "N3atomic", "N3twopass", "N3bwd"][c.newton3] if 0 <= c.newton3 <= 3 else f"n3={c.newton3}"
@@ -72,6 +73,9 @@ _SIGS = {
     "lj_update_positions": (C.c_int, [_VP, _VP, C.c_int32]),
     "lj_bin_cells": (C.c_int, [_VP, C.c_int32]),
     "lj_build_verlet": (C.c_int, [_VP, C.c_int32]),
+    "lj_build_clusters": (C.c_int, [_VP, C.c_int32, C.c_int32]),
+    "lj_get_clusters": (C.c_int, [_VP, C.POINTER(C.c_int64), _VP, C.POINTER(C.c_int32)]),
+    "lj_get_cluster_lists": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int32)]),
     "lj_compute_forces": (C.c_int, [_VP, lj_config, _VP, _VP]),
     "lj_config_valid": (C.c_int32, [lj_config]),
     "lj_config_list": (C.c_int32, [_VP, C.c_int32]),
@@ -247,6 +251,10 @@ class Domain:
     def build_verlet(self, half=False):
         self._check(self.lib.lj_build_verlet(self.h, int(bool(half))))
 
+    def build_clusters(self, M, half=False):
+        """Cluster order and cluster-pair lists for cluster size M (4, 6 or 8)."""
+        self._check(self.lib.lj_build_clusters(self.h, int(M), int(bool(half))))
+
     def compute_forces(self, cfg, energy=False):
         """One force evaluation; with energy=True returns (U, W)."""
         if energy:
@@ -298,6 +306,25 @@ class Domain:
         nn = np.zeros(self.n, dtype=np.int32)
         self._check(self.lib.lj_get_verlet(self.h, nbr.ctypes.data, nn.ctypes.data, C.byref(cap)))
         return nbr, nn
+
+    def clusters(self):
+        """(cl_start (ncl + 1,), n_t) of the current cluster order."""
+        ncl, nt = C.c_int64(), C.c_int32()
+        self._check(self.lib.lj_get_clusters(self.h, C.byref(ncl), None, C.byref(nt)))
+        cs = np.zeros(ncl.value + 1, dtype=np.uint32)
+        self._check(self.lib.lj_get_clusters(self.h, C.byref(ncl), cs.ctypes.data, C.byref(nt)))
+        return cs, nt.value
+
+    def cluster_lists(self):
+        """Neighbour cluster indices per cluster (a list of int32 arrays, library order)."""
+        cs, _ = self.clusters()
+        ncl = len(cs) - 1
+        cap = C.c_int32()
+        self._check(self.lib.lj_get_cluster_lists(self.h, None, None, C.byref(cap)))
+        nbr = np.zeros((max(ncl, 1), cap.value), dtype=np.int32)
+        nn = np.zeros(max(ncl, 1), dtype=np.int32)
+        self._check(self.lib.lj_get_cluster_lists(self.h, nbr.ctypes.data, nn.ctypes.data, C.byref(cap)))
+        return [nbr[I, :nn[I]].copy() for I in range(ncl)]
 
     def counters(self):
         c = np.zeros(5, dtype=np.int64)
