@@ -472,7 +472,10 @@ lj_status run_force(Ctx& c, const lj_config& cfg, bool ev, bool acc_zeroed = fal
   if (t1) CK(cudaEventRecord(t1, c.stream));
   CK(e);
   c.launches += force_launches(c, cfg, c.tiles_gen != tiles_before || c.tiles_T != tiles_T_before);
-  if (!(cfg.container == LJ_VL && cfg.newton3 == LJ_N3_OFF)) {  // fused into the VL N3-off store
+  if (cfg.newton3 == LJ_N3_ATOMIC || cfg.newton3 == LJ_N3_ATOMIC_BWD) {  // unscaled atomic sums
+    CK(launch_scale_check(c));
+    c.launches += 1;
+  } else if (!(cfg.container == LJ_VL && cfg.newton3 == LJ_N3_OFF)) {  // fused into the VL N3-off store
     CK(launch_check_finite(c));
     c.launches += 1;
   }

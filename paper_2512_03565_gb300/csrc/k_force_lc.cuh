@@ -27,8 +27,9 @@
 //
 // Forces are accumulated per lane in the pair precision R over one tile (one
 // particle's pairs of this evaluation) and folded once into FP64 (f2d_exact,
-// one FP64 multiply by 24 eps / u); energy and virial likewise, then reduced
-// in FP64 per block.
+// one FP64 multiply by 24 eps / u; with Newton-3 the unscaled sums are added
+// by atomics and scaled once per particle afterwards); energy and virial
+// likewise, then reduced in FP64 per block.
 #pragma once
 #include "ljgb_internal.cuh"
 
@@ -127,10 +128,14 @@ __device__ __forceinline__ bool seg_ok(int kind, uint32_t j, uint32_t i, uint32_
   return kind == 1 ? (j > i) : (cxi == (uint32_t)(nc - 1));
 }
 
-// Add v (R) times scale to an FP64 array element with an atomic.
+// Add v (R, exactly converted) to an FP64 array element with an atomic.
+// Newton-3 evaluations accumulate the unscaled sums this way (+ for a j, - for
+// an i) and the factor 24 eps / u is applied once per particle afterwards
+// (launch_scale_check): one FP64 multiply per contribution would otherwise run
+// on GB300's narrow FP64 pipe.
 template <typename R>
-__device__ __forceinline__ void atomic_add_scaled(double* p, R v, double scale) {
-  if (v != (R)0) atomicAdd(p, scale * Prec<R>::to_d(v));
+__device__ __forceinline__ void atomic_add_raw(double* p, R v) {
+  if (v != (R)0) atomicAdd(p, Prec<R>::to_d(v));
 }
 
 struct LCArgs {
@@ -222,9 +227,9 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
           }
         }
         if (N3 && lane < (int)m) {
-          atomic_add_scaled(out.fx + jb + lane, gx, P.e24u);
-          atomic_add_scaled(out.fy + jb + lane, gy, P.e24u);
-          atomic_add_scaled(out.fz + jb + lane, gz, P.e24u);
+          atomic_add_raw(out.fx + jb + lane, gx);
+          atomic_add_raw(out.fy + jb + lane, gy);
+          atomic_add_raw(out.fz + jb + lane, gz);
         }
         __syncwarp();
       }
@@ -233,9 +238,9 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
     for (int k = 0; k < K; ++k) {
       if (!vi[k]) continue;
       if (N3) {
-        atomic_add_scaled(out.fx + ii[k], fx[k], -P.e24u);
-        atomic_add_scaled(out.fy + ii[k], fy[k], -P.e24u);
-        atomic_add_scaled(out.fz + ii[k], fz[k], -P.e24u);
+        atomic_add_raw(out.fx + ii[k], -fx[k]);
+        atomic_add_raw(out.fy + ii[k], -fy[k]);
+        atomic_add_raw(out.fz + ii[k], -fz[k]);
       } else {
         out.fx[ii[k]] = -P.e24u * Prec<R>::to_d(fx[k]);
         out.fy[ii[k]] = -P.e24u * Prec<R>::to_d(fy[k]);
@@ -398,9 +403,9 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
           if ((q & 31u) == 31u || q + 1 == m) {
             const uint32_t qb = q & ~31u;
             if (lane <= (int)(q - qb)) {
-              atomic_add_scaled(out.fx + jb + qb + lane, gx, P.e24u);
-              atomic_add_scaled(out.fy + jb + qb + lane, gy, P.e24u);
-              atomic_add_scaled(out.fz + jb + qb + lane, gz, P.e24u);
+              atomic_add_raw(out.fx + jb + qb + lane, gx);
+              atomic_add_raw(out.fy + jb + qb + lane, gy);
+              atomic_add_raw(out.fz + jb + qb + lane, gz);
             }
             gx = gy = gz = 0;
           }
@@ -414,9 +419,9 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
     if (failed) break;
     if (vi) {
       if (N3) {
-        atomic_add_scaled(out.fx + ii, fx, -P.e24u);
-        atomic_add_scaled(out.fy + ii, fy, -P.e24u);
-        atomic_add_scaled(out.fz + ii, fz, -P.e24u);
+        atomic_add_raw(out.fx + ii, -fx);
+        atomic_add_raw(out.fy + ii, -fy);
+        atomic_add_raw(out.fz + ii, -fz);
       } else {
         out.fx[ii] = -P.e24u * Prec<R>::to_d(fx);
         out.fy[ii] = -P.e24u * Prec<R>::to_d(fy);
@@ -491,17 +496,17 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
           }
         }
         if (N3 && lane < (int)m) {
-          atomic_add_scaled(out.fx + jb + lane, gx, P.e24u);
-          atomic_add_scaled(out.fy + jb + lane, gy, P.e24u);
-          atomic_add_scaled(out.fz + jb + lane, gz, P.e24u);
+          atomic_add_raw(out.fx + jb + lane, gx);
+          atomic_add_raw(out.fy + jb + lane, gy);
+          atomic_add_raw(out.fz + jb + lane, gz);
         }
       }
     }
     if (vi) {
       if (N3) {
-        atomic_add_scaled(out.fx + ii, fx, -P.e24u);
-        atomic_add_scaled(out.fy + ii, fy, -P.e24u);
-        atomic_add_scaled(out.fz + ii, fz, -P.e24u);
+        atomic_add_raw(out.fx + ii, -fx);
+        atomic_add_raw(out.fy + ii, -fy);
+        atomic_add_raw(out.fz + ii, -fz);
       } else {
         out.fx[ii] = -P.e24u * Prec<R>::to_d(fx);
         out.fy[ii] = -P.e24u * Prec<R>::to_d(fy);
@@ -557,9 +562,9 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
           fy += fac * bf;
           fz += fac * cf_;
           if (N3) {
-            atomic_add_scaled(out.fx + j, fac * af, P.e24u);
-            atomic_add_scaled(out.fy + j, fac * bf, P.e24u);
-            atomic_add_scaled(out.fz + j, fac * cf_, P.e24u);
+            atomic_add_raw(out.fx + j, fac * af);
+            atomic_add_raw(out.fy + j, fac * bf);
+            atomic_add_raw(out.fz + j, fac * cf_);
           }
         }
       }
@@ -572,9 +577,9 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
     }
     if (vi && sub == 0) {
       if (N3) {
-        atomic_add_scaled(out.fx + ii, fx, -P.e24u);
-        atomic_add_scaled(out.fy + ii, fy, -P.e24u);
-        atomic_add_scaled(out.fz + ii, fz, -P.e24u);
+        atomic_add_raw(out.fx + ii, -fx);
+        atomic_add_raw(out.fy + ii, -fy);
+        atomic_add_raw(out.fz + ii, -fz);
       } else {
         out.fx[ii] = -P.e24u * Prec<R>::to_d(fx);
         out.fy[ii] = -P.e24u * Prec<R>::to_d(fy);

@@ -12,7 +12,8 @@
 //             and one j position per lane (both broadcast within the lane's
 //             j-slot group).  The i force is reduced over the j-slots at the
 //             end of the list; with Newton-3 the j force of each pass is
-//             reduced over the M i lanes and added by one FP64 atomic.
+//             reduced over the M i lanes and added by one FP64 atomic (the
+//             unscaled sum; the factor 24 eps / u follows per particle).
 //   CL_JLANE  lane = j-slot (32 j's per pass, from 32/M neighbour clusters);
 //             the M i's are held in every lane's registers and visited in
 //             turn.  The j force stays in its lane (Newton-3: one atomic per j
@@ -39,17 +40,21 @@ struct VclArgs {
   int cap;
 };
 
+// Without Newton-3 a particle's force is stored once, scaled by -24 eps / u.
+// With it, the unscaled sums are added by atomics (+ for a j, - for an i) and
+// scaled once per particle afterwards (launch_scale_check).
 template <typename R>
-__device__ __forceinline__ void store_or_add(const ForceOut& out, uint32_t i, R fx, R fy, R fz, double s, bool n3) {
-  if (n3) {
-    if (fx != (R)0) atomicAdd(out.fx + i, s * Prec<R>::to_d(fx));
-    if (fy != (R)0) atomicAdd(out.fy + i, s * Prec<R>::to_d(fy));
-    if (fz != (R)0) atomicAdd(out.fz + i, s * Prec<R>::to_d(fz));
-  } else {
-    out.fx[i] = s * Prec<R>::to_d(fx);
-    out.fy[i] = s * Prec<R>::to_d(fy);
-    out.fz[i] = s * Prec<R>::to_d(fz);
-  }
+__device__ __forceinline__ void store_force(const ForceOut& out, uint32_t i, R fx, R fy, R fz, double s) {
+  out.fx[i] = s * Prec<R>::to_d(fx);
+  out.fy[i] = s * Prec<R>::to_d(fy);
+  out.fz[i] = s * Prec<R>::to_d(fz);
+}
+
+template <typename R>
+__device__ __forceinline__ void add_force(const ForceOut& out, uint32_t i, R fx, R fy, R fz) {
+  if (fx != (R)0) atomicAdd(out.fx + i, Prec<R>::to_d(fx));
+  if (fy != (R)0) atomicAdd(out.fy + i, Prec<R>::to_d(fy));
+  if (fz != (R)0) atomicAdd(out.fz + i, Prec<R>::to_d(fz));
 }
 
 template <typename R, int M, bool N3, bool EV>
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(256) k_vcl_tile(LJParams P, VclArgs A, ForceOu
             hz += tz;
           }
         }
-        if (ii == 0 && vj) store_or_add<R>(out, j, hx, hy, hz, P.e24u, true);
+        if (ii == 0 && vj) add_force<R>(out, j, hx, hy, hz);
       }
     }
     // the i force: sum over the j-slots
@@ -123,7 +128,10 @@ __global__ void __launch_bounds__(256) k_vcl_tile(LJParams P, VclArgs A, ForceOu
       fy = sy;
       fz = sz;
     }
-    if (vi && js == 0) store_or_add<R>(out, i, fx, fy, fz, -P.e24u, N3);
+    if (vi && js == 0) {
+      if (N3) add_force<R>(out, i, -fx, -fy, -fz);
+      else store_force<R>(out, i, fx, fy, fz, -P.e24u);
+    }
     if (EV) {
       eu_d += Prec<R>::to_d(eu);
       ew_d += Prec<R>::to_d(ew);
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(256) k_vcl_jlane(LJParams P, VclArgs A, ForceO
           gz += fac * cf;
         }
       }
-      if (N3 && vj) store_or_add<R>(out, j, gx, gy, gz, P.e24u, true);
+      if (N3 && vj) add_force<R>(out, j, gx, gy, gz);
     }
 #pragma unroll
     for (int k = 0; k < M; ++k) {
@@ -188,7 +196,10 @@ __global__ void __launch_bounds__(256) k_vcl_jlane(LJParams P, VclArgs A, ForceO
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
       }
-      if (lane == 0 && (uint32_t)k < ni) store_or_add<R>(out, ib + k, sx, sy, sz, -P.e24u, N3);
+      if (lane == 0 && (uint32_t)k < ni) {
+        if (N3) add_force<R>(out, ib + k, -sx, -sy, -sz);
+        else store_force<R>(out, ib + k, sx, sy, sz, -P.e24u);
+      }
     }
     if (EV) {
       eu_d += Prec<R>::to_d(eu);

@@ -50,9 +50,11 @@ __device__ __forceinline__ void vl_store(const ForceOut& out, uint32_t* status, 
   if (!isfinite(f0 + f1 + f2)) atomicOr(status, ST_NONFINITE);
 }
 
+// Newton-3: the unscaled sum is added (the factor 24 eps / u follows once per
+// particle, launch_scale_check)
 template <typename R>
-__device__ __forceinline__ void vl_atomic(double* p, R v, double scale) {
-  if (v != (R)0) atomicAdd(p, scale * Prec<R>::to_d(v));
+__device__ __forceinline__ void vl_atomic(double* p, R v) {
+  if (v != (R)0) atomicAdd(p, Prec<R>::to_d(v));
 }
 
 // Entries are processed in batches of VL_BATCH: the batch's list entries are
@@ -98,9 +100,9 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
           fy += fac * bf;
           fz += fac * cf;
           if (N3 == 1) {
-            vl_atomic(out.fx + jc[t], fac * af, P.e24u);
-            vl_atomic(out.fy + jc[t], fac * bf, P.e24u);
-            vl_atomic(out.fz + jc[t], fac * cf, P.e24u);
+            vl_atomic(out.fx + jc[t], fac * af);
+            vl_atomic(out.fy + jc[t], fac * bf);
+            vl_atomic(out.fz + jc[t], fac * cf);
           } else if (N3 == 2) {
             if (k0 + t < m) {
               const int64_t e = (int64_t)(k0 + t) * n + i;
@@ -116,9 +118,9 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
         for (int t = 0; t < VL_BATCH; ++t) jc[t] = jn[t];
       }
       if (N3 == 1) {
-        vl_atomic(out.fx + i, fx, -P.e24u);
-        vl_atomic(out.fy + i, fy, -P.e24u);
-        vl_atomic(out.fz + i, fz, -P.e24u);
+        vl_atomic(out.fx + i, -fx);
+        vl_atomic(out.fy + i, -fy);
+        vl_atomic(out.fz + i, -fz);
       } else {
         vl_store(out, A.status, i, -P.e24u * Prec<R>::to_d(fx), -P.e24u * Prec<R>::to_d(fy),
                  -P.e24u * Prec<R>::to_d(fz));
@@ -180,9 +182,9 @@ __global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, Forc
           fy += fac * bf;
           fz += fac * cf;
           if (N3 == 1) {
-            vl_atomic(out.fx + jc[t], fac * af, P.e24u);
-            vl_atomic(out.fy + jc[t], fac * bf, P.e24u);
-            vl_atomic(out.fz + jc[t], fac * cf, P.e24u);
+            vl_atomic(out.fx + jc[t], fac * af);
+            vl_atomic(out.fy + jc[t], fac * bf);
+            vl_atomic(out.fz + jc[t], fac * cf);
           }
         }
 #pragma unroll
@@ -197,9 +199,9 @@ __global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, Forc
     }
     if (vi && sub == 0) {
       if (N3 == 1) {
-        vl_atomic(out.fx + i, fx, -P.e24u);
-        vl_atomic(out.fy + i, fy, -P.e24u);
-        vl_atomic(out.fz + i, fz, -P.e24u);
+        vl_atomic(out.fx + i, -fx);
+        vl_atomic(out.fy + i, -fy);
+        vl_atomic(out.fz + i, -fz);
       } else {
         vl_store(out, A.status, i, -P.e24u * Prec<R>::to_d(fx), -P.e24u * Prec<R>::to_d(fy),
                  -P.e24u * Prec<R>::to_d(fz));

@@ -206,6 +206,24 @@ cudaError_t launch_check_finite(Ctx& c) {
   return cudaGetLastError();
 }
 
+// f *= scale, then the finiteness check: the Newton-3 kernels leave unscaled
+// FP64 sums (one multiply per particle here instead of one per contribution).
+__global__ void k_scale_check(double* __restrict__ f, int64_t m, double scale, uint32_t* __restrict__ status) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = f[i] * scale;
+    f[i] = v;
+    bad |= !isfinite(v);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+cudaError_t launch_scale_check(Ctx& c) {
+  k_scale_check<<<std::min<unsigned>(nb(3 * c.n, 256), 1024), 256, 0, c.stream>>>(c.frc, 3 * c.n, c.P.e24u,
+                                                                                   c.status);
+  return cudaGetLastError();
+}
+
 // Pair set of the linked-cell scan: every (i, j) with orig(i) < orig(j),
 // 0 < R^2 <= Rc2, j in the 27 cells around i.  With out == nullptr only counts.
 __global__ void k_lc_pairs(const uint4* __restrict__ pos, const uint32_t* __restrict__ cs, int nc, int64_t n,

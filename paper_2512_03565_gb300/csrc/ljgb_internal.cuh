@@ -486,6 +486,7 @@ cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, 
 cudaError_t launch_feature_stats(Ctx& c, unsigned long long* stats);
 cudaError_t launch_ke(Ctx& c, double* out);
 cudaError_t launch_check_finite(Ctx& c);
+cudaError_t launch_scale_check(Ctx& c);
 cudaError_t launch_lc_pairs(Ctx& c, unsigned long long* count, int2* out, size_t cap);
 
 }  // namespace ljgb

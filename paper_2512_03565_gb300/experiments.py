@@ -20,11 +20,17 @@
 
 * ``ensemble-launch``: one direct launch of the list-mode batch (for ncu).
 
+* ``clusters``: Verlet cluster lists (Sec. 5.1's cluster-size dimension):
+  per cluster size and order, the force-kernel time on fixed lists, the
+  tuning-cost time (rebuild amortised) and the candidate pairs per particle,
+  beside the particle Verlet lists, on fluid, slab, dilute gas and FCC solid.
+
 * ``traversal``: the linked-cell Newton-3 orders with the forward and the
   backward half shell (the two roles a cell can take in a cell pair, Sec.
   5.1) on homogeneous, slab and solid systems, in both pair precisions.
 
-Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy|traversal [options]
+Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy|traversal|clusters
+       [options]
 """
 from __future__ import annotations
 
@@ -258,10 +264,56 @@ def traversal(n=500_000, samples=5, log=print):
     return out
 
 
+def clusters(samples=5, evals=20, log=print):
+    """Sec. 5.1, cluster sizes: every cluster-list configuration (orders
+    CL_TILE / CL_JLANE, M = 4, 6, 8, Newton-3 off / atomic) against the best
+    particle Verlet-list configuration.  Per system: full-search times
+    (rebuild amortised), force-kernel time on fixed lists (CUDA events over
+    `evals` evaluations), and the candidate pairs per particle that the
+    cluster lists hand to the kernel (sum over cluster pairs of |I| |J|,
+    full lists) against the particle lists' entries."""
+    systems = [W.config2(), W.slab(500_000, 0.8, 0.02, 0.5, W.BASE_SEED + 91),
+               W.stratified(500_000, 0.1, W.BASE_SEED + 92), W.fcc(500_000, 1.0, W.BASE_SEED + 93)]
+    out = []
+    for s in systems:
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos, s.vel)
+        _, times = d.tune(0, samples)
+        vl = {k: v for k, v in times.items() if k.startswith("VL:")}
+        best_vl = min(vl, key=vl.get)
+        kernel = {}
+        cfgs = [c for c in lj.configs() if c.container == lj.LJ_VCL]
+        by_name = {lj.config_name(c): c for c in lj.configs()}
+        for cfg in [by_name[best_vl]] + cfgs:
+            d.compute_forces(cfg)
+            d.timing(1)
+            for _ in range(evals):
+                d.compute_forces(cfg)
+            ms, n, _ = d.timing(0)
+            kernel[lj.config_name(cfg)] = ms / max(n, 1)
+        cand = {}
+        for M in (4, 6, 8):
+            d.build_clusters(M, 0)
+            cs, _ = d.clusters()
+            sizes = np.diff(cs).astype(np.int64)
+            lists = d.cluster_lists()
+            cand[M] = float(sum(sizes[I] * sizes[l].sum() for I, l in enumerate(lists)) / s.n)
+        d.build_verlet(0)
+        _, nn = d.verlet()
+        r = {"system": s.name, "n": s.n, "best_vl": best_vl, "times_ms": times, "kernel_ms": kernel,
+             "cluster_candidates_per_particle": cand, "verlet_entries_per_particle": float(nn.mean())}
+        out.append(r)
+        vcl = {k: v for k, v in kernel.items() if k.startswith("VCL:")}
+        bv = min(vcl, key=vcl.get)
+        log(f"{s.name}: VL {best_vl} kernel {kernel[best_vl]:.4f} ms; best VCL {bv} {vcl[bv]:.4f} ms; "
+            f"candidates/particle {cand} vs VL entries {nn.mean():.1f}")
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy",
-                                     "traversal"])
+                                     "traversal", "clusters"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--data", default="gpurun_out/tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
@@ -306,6 +358,10 @@ def main(argv=None):
         ens.run(0.002, a.steps, use_graph=False)
         print(json.dumps({"steps": a.steps, "ms_per_step": (time.perf_counter() - t0) / max(1, a.steps) * 1e3}))
         ens.close()
+    elif a.what == "clusters":
+        res = clusters()
+        if a.out:
+            json.dump(res, open(a.out, "w"))
     elif a.what == "traversal":
         res = traversal()
         if a.out:
