@@ -207,12 +207,12 @@ def verlet(pos, L, rl, nc, half, cap):
 
 
 def vcl_ntower(n, M) -> int:
-    """Towers per axis of the cluster grid (reading R5): the largest k >= 1 with k^3 M <= n."""
+    """Towers per axis of the cluster grid (reading R19): the largest k >= 1 with k^3 M <= n."""
     return int(_load().orc_vcl_ntower(int(n), int(M)))
 
 
 def vcl_order(pos, M):
-    """Cluster order (reading R5).  Returns (perm, cl_start): perm[k] is the
+    """Cluster order (reading R19).  Returns (perm, cl_start): perm[k] is the
     original index of the k-th particle in cluster order, cluster c holds
     perm[cl_start[c]:cl_start[c+1]]."""
     x, y, z = _soa(pos)
@@ -226,7 +226,7 @@ def vcl_order(pos, M):
 
 
 def vcl_lists(pos, L, rl, M, half):
-    """Cluster-pair lists by brute force over all cluster pairs (reading R5).
+    """Cluster-pair lists by brute force over all cluster pairs (reading R19).
     Returns (perm, cl_start, lists): lists[I] the ascending neighbour clusters of I."""
     x, y, z = _soa(pos)
     perm, cls = vcl_order(pos, M)

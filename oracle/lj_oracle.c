@@ -36,7 +36,7 @@
  *      is stable (ties keep ascending original index).
  *   R4 Verlet-list order: the 9 (dz,dy) rows in lexicographic order, inside a
  *      row ascending sorted index; half lists keep only j > i (sorted index).
- *   R5 Verlet cluster lists: towers, cluster order, boxes and the cluster
+ *   R19 Verlet cluster lists: towers, cluster order, boxes and the cluster
  *      neighbour rule, stated at orc_vcl_order below.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused.
@@ -365,7 +365,7 @@ int orc_verlet(int64_t n, const uint32_t* x, const uint32_t* y, const uint32_t* 
 /* ------------------------------------------------------------------------ */
 /* Verlet cluster lists (Sec. 2.1.1: clusters of a fixed number of nearby    */
 /* particles, with neighbour lists of whole clusters rebuilt every few steps; */
-/* Sec. 5.1: cluster sizes 4, 6 and 8).  Reading R5:                         */
+/* Sec. 5.1: cluster sizes 4, 6 and 8).  Reading R19:                        */
 /*   - towers: n_t x n_t columns over (x, y), n_t the largest k >= 1 with    */
 /*     k^3 M <= n (so a tower cell holds about M particles and a cluster is  */
 /*     about as tall as it is wide); column of a particle                    */
@@ -437,7 +437,7 @@ static inline uint64_t interval_gap(uint32_t a0, uint32_t a1, uint32_t b0, uint3
   return g1 < g2 ? g1 : g2;
 }
 
-/* Cluster-pair lists by brute force over all cluster pairs (reading R5).
+/* Cluster-pair lists by brute force over all cluster pairs (reading R19).
  * perm / cl_start as from orc_vcl_order; x, y, z in original order.  nbr is
  * row-major [ncl][cap] of cluster indices in ascending order, nn[ncl] the
  * complete list lengths (entries beyond cap are dropped).  Returns 0, 1 if a

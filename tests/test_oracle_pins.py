@@ -285,7 +285,7 @@ def test_bin_cells_is_stable_counting_sort(orc):
         assert orc.cell_of((xv, 0, 0), nc) == (xv * nc) // TWO32
 
 
-# --- Verlet cluster lists (Sec. 2.1.1; cluster sizes of Sec. 5.1; reading R5) ---
+# --- Verlet cluster lists (Sec. 2.1.1; cluster sizes of Sec. 5.1; reading R19) --
 
 @pytest.mark.parametrize("n,M,k", [(1, 4, 1), (3, 4, 1), (1000, 4, 6), (1048576, 4, 64), (1048576, 8, 50),
                                    (1048576, 6, 55), (2000000, 8, 62)])
