@@ -41,13 +41,17 @@ __device__ __forceinline__ int vl_entry(const VLArgs& A, int64_t e, int64_t i, i
   return __ldcs(A.nbr + e);
 }
 
-// Stores the FP64 force of particle i; a non-finite result sets ST_NONFINITE.
+// Stores the FP64 force of particle i; a non-finite component sets
+// ST_NONFINITE (tested on the exponent bits, off GB300's narrow FP64 pipe).
 __device__ __forceinline__ void vl_store(const ForceOut& out, uint32_t* status, int64_t i, double f0, double f1,
                                          double f2) {
   out.fx[i] = f0;
   out.fy[i] = f1;
   out.fz[i] = f2;
-  if (!isfinite(f0 + f1 + f2)) atomicOr(status, ST_NONFINITE);
+  const uint32_t E = 0x7ff00000u;
+  const bool bad = ((uint32_t)__double2hiint(f0) & E) == E || ((uint32_t)__double2hiint(f1) & E) == E ||
+                   ((uint32_t)__double2hiint(f2) & E) == E;
+  if (bad) atomicOr(status, ST_NONFINITE);
 }
 
 // Newton-3: the unscaled sum is added (the factor 24 eps / u follows once per

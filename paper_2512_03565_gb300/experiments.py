@@ -87,9 +87,11 @@ def leave_one_out(X, T, box_ids, names, epochs=2000, lr=3e-3, default="VL:JSPLIT
     for b in np.unique(box_ids):
         tr, te = box_ids != b, box_ids == b
         model = tuner.train(X[tr], T[tr], epochs=epochs, lr=lr)
+        cols = np.where(model["keep"])[0]
         pred = tuner.predict(model, X[te])
         for r, row in enumerate(np.where(te)[0]):
-            reg, k = regret_of(pred[r], T[row], M[row])
+            reg, kk = regret_of(pred[r], T[row, cols], M[row, cols])
+            k = int(cols[kk])
             best = np.nanmin(np.where(M[row], T[row], np.nan))
             dflt = T[row, d_idx] / best if d_idx is not None and M[row, d_idx] else float("nan")
             res.append({"box": int(b), "row": int(row), "learned_regret": float(reg),
@@ -323,16 +325,18 @@ def main(argv=None):
     ap.add_argument("--phase", type=int, default=500)
     ap.add_argument("--radius", type=float, default=84.19)
     ap.add_argument("--loo", action="store_true")
+    ap.add_argument("--samples", type=int, default=3, help="timed evaluations per configuration (sweep)")
     a = ap.parse_args(argv)
     from . import build as B
     B.build()
     if a.what == "sweep":
-        density_sweep(scale=a.scale, out=a.data)
+        density_sweep(scale=a.scale, samples=a.samples, out=a.data)
     elif a.what == "train":
         z = np.load(a.data)
         X, T, names, box = z["X"], z["T"], [str(v) for v in z["names"]], z["box"]
         model = tuner.train(X, T, epochs=a.epochs)
         tuner.save(model, names, a.model, meta={"rows": int(X.shape[0]), "epochs": a.epochs,
+                                                "configs_timed": len(names), "outputs": int(model["C"]),
                                                 "final_loss": float(model["losses"][-1])})
         print(f"trained: rows={X.shape[0]} loss {model['losses'][0]:.4f} -> {model['losses'][-1]:.4f}")
         if a.loo:

@@ -9,7 +9,8 @@ inference runs inside lj_tune kind 1.
 
 Targets are per-row relative log times, log(t_config / t_best), so the network
 ranks configurations; missing or invalid configurations are masked out of the
-loss.  Features are standardised with the training set's mean and standard
+loss.  The network's outputs are the configurations that come within 25 % of
+the best in at least one training row.  Features are standardised with the training set's mean and standard
 deviation (stored with the model).
 """
 from __future__ import annotations
@@ -65,8 +66,21 @@ def targets(T):
     return Y, mask.astype(np.float64)
 
 
-def train(X, T, epochs=3000, lr=3e-3, seed=0):
-    """Trains the network on the GPU.  Returns the model dict."""
+def candidates(T, near=1.25):
+    """Configurations within `near` of some row's best in the timings T: the
+    only ones the network ranks (it has no evidence that the others ever win,
+    and each extra output is one more chance of a wrong pick on a system
+    unlike the training data)."""
+    Y, M = targets(T)
+    return (np.where(M > 0, Y, np.inf) <= math.log(near)).any(axis=0)
+
+
+def train(X, T, epochs=3000, lr=3e-3, seed=0, near=1.25):
+    """Trains the network on the GPU over the candidate configurations of T
+    (see `candidates`).  Returns the model dict; model["keep"] marks T's
+    columns that are the network's outputs, in order."""
+    keep = candidates(T, near)
+    T = T[:, keep]
     Y, M = targets(T)
     mean = X.mean(axis=0)
     std = X.std(axis=0)
@@ -85,7 +99,7 @@ def train(X, T, epochs=3000, lr=3e-3, seed=0):
         off += k
     params, losses = lj.mlp_train(p0, Cn, Xs, Y, M, epochs, lr)
     return {"params": params.astype(np.float32), "mean": mean.astype(np.float32),
-            "std": std.astype(np.float32), "C": Cn, "losses": losses}
+            "std": std.astype(np.float32), "C": Cn, "losses": losses, "keep": keep}
 
 
 def predict(model, X):
@@ -94,8 +108,11 @@ def predict(model, X):
 
 
 def save(model, names, path=MODEL_PATH, meta=None):
+    """Saves the model with the names of its outputs (the kept columns of `names`)."""
+    keep = model.get("keep")
+    out_names = list(names) if keep is None else [n for n, k in zip(names, keep) if k]
     np.savez(path, params=model["params"], mean=model["mean"], std=model["std"], C=int(model["C"]),
-             names=np.array(names), losses=model.get("losses", np.zeros(1)),
+             names=np.array(out_names), losses=model.get("losses", np.zeros(1)),
              meta=json.dumps(meta or {}))
 
 
