@@ -317,7 +317,7 @@ def main(argv=None):
     ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy",
                                      "traversal", "clusters"])
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--data", default="gpurun_out/tuner_data.npz")
+    ap.add_argument("--data", default="tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
     ap.add_argument("--out", default=None)
     ap.add_argument("--epochs", type=int, default=3000)
