@@ -177,6 +177,15 @@ __device__ void ens_scan_tile(const uint32_t* in, uint32_t* out, int64_t n, int6
   __syncthreads();
 }
 
+// One atomic per warp and force phase for the pair counter (a per-iteration
+// atomic on the single counter serialised in L2).
+__device__ __forceinline__ void flush_pairs(const EnsArgs& A, uint32_t pairs) {
+  unsigned long long wc = pairs;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
+  if ((threadIdx.x & 31) == 0 && wc) atomicAdd(A.npairs, wc);
+}
+
 template <int W>
 __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __restrict__ pos,
                                            const uint32_t* __restrict__ cs, double* __restrict__ fx) {
@@ -184,6 +193,7 @@ __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __rest
   const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n = A.ntot;
+  uint32_t pairs = 0;  // this lane's in-cutoff pairs of the phase, added once per warp at its end
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * G < n; w += nwarps) {
     const int64_t i = w * G + g;
     const bool vi = i < n;
@@ -231,10 +241,7 @@ __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __rest
       ay += __shfl_xor_sync(0xffffffffu, ay, o);
       az += __shfl_xor_sync(0xffffffffu, az, o);
     }
-    unsigned long long wc = (unsigned long long)cnt;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
-    if (lane == 0 && wc) atomicAdd(A.npairs, wc);
+    pairs += (uint32_t)cnt;
     if (vi && sub == 0) {
       const double f0 = -B.e24u * f2d_exact(ax), f1 = -B.e24u * f2d_exact(ay), f2 = -B.e24u * f2d_exact(az);
       fx[i] = f0;
@@ -243,6 +250,7 @@ __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __rest
       if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2)) atomicOr(A.status, ST_NONFINITE);
     }
   }
+  flush_pairs(A, pairs);
 }
 
 // Forces over the Verlet lists (JSPLIT<W>: W lanes per particle stride over
@@ -255,6 +263,7 @@ __device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __r
   const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n = A.ntot;
+  uint32_t pairs = 0;  // this lane's in-cutoff pairs of the phase, added once per warp at its end
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * G < n; w += nwarps) {
     const int64_t i = w * G + g;
     const bool vi = i < n;
@@ -290,10 +299,7 @@ __device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __r
       ay += __shfl_xor_sync(0xffffffffu, ay, o);
       az += __shfl_xor_sync(0xffffffffu, az, o);
     }
-    unsigned long long wc = (unsigned long long)cnt;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
-    if (lane == 0 && wc) atomicAdd(A.npairs, wc);
+    pairs += (uint32_t)cnt;
     if (vi && sub == 0) {
       const double f0 = -B.e24u * f2d_exact(ax), f1 = -B.e24u * f2d_exact(ay), f2 = -B.e24u * f2d_exact(az);
       fx[i] = f0;
@@ -302,6 +308,7 @@ __device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __r
       if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2)) atomicOr(A.status, ST_NONFINITE);
     }
   }
+  flush_pairs(A, pairs);
 }
 
 // The list build of every box: one warp per cell of the list grid, the cell's
