@@ -139,7 +139,7 @@ lj_status lj_set_particles_fp(lj_ctx* ctx, int64_t n, const uint32_t* pos_fp, co
 
 /* New positions for the loaded particles (caller's order, n as loaded,
  * float64 [3][n], host or device), velocities kept.  Unlike lj_set_particles
- * the cell order and the Verlet lists are kept: the next force evaluation
+ * the cell (or cluster) order and the Verlet (or cluster) lists are kept: the next force evaluation
  * reuses the lists while every particle stays within skin/2 of its position
  * at the last build and rebuilds them otherwise (Sec. 2.1.1: lists are kept
  * over several steps thanks to the skin); linked cells are rebinned.  This
@@ -206,8 +206,8 @@ int32_t lj_config_list(lj_config* out, int32_t cap);
 
 /* nsteps of velocity Verlet (Sec. 2.1): v += dt/(2m) F; x += v dt (fixed
  * point, rounded to nearest, periodic wrap); F = F(x) with cfg; v += dt/(2m) F.
- * Verlet lists are rebuilt every rebuild_every steps (and early when a particle
- * moved more than skin/2).  Computes the initial forces if none are current.
+ * Verlet and cluster lists are rebuilt every rebuild_every steps (and early
+ * when a particle moved more than skin/2).  Computes the initial forces if none are current.
  * The last step's closing half kick is kept pending on the device and applied
  * by the next call's first kick (as a separate FMA, so the arithmetic is that
  * of unfused kicks), or first thing by lj_get_state, lj_kinetic_energy and any
@@ -307,7 +307,9 @@ lj_status lj_get_state(lj_ctx* ctx, uint32_t* pos_fp, double* vel, int32_t on_de
 lj_status lj_get_pairs(lj_ctx* ctx, int32_t container, int64_t* n_pairs, int32_t* ij);
 
 /* The current cell order: perm[k] = original index of the k-th particle
- * (n entries) and cell_start (n_c^3 + 1 entries, n_c of the last binning).
+ * (n entries) and cell_start (n_c^3 + 1 entries, n_c of the last binning;
+ * after a cluster build the cells are the towers' z-slabs, id (cx n_t + cy)
+ * n_t + cz, and n_c = n_t).
  * Host pointers; either may be NULL.  *nc_out (may be NULL) gets n_c. */
 lj_status lj_get_cells(lj_ctx* ctx, uint32_t* perm, uint32_t* cell_start, int32_t* nc_out);
 
