@@ -191,7 +191,8 @@ def run_reference(args, ws, rank, pg):
     value = float(np.sum(pairs) / np.sum(times))
     line = {
         "impl": "reference", "metric": "LJ in-cutoff pair evals/s", "value": value, "unit": "pairs/s",
-        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "n_gpus": ws, "gpus_used": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD + "; reference step = one FP64 linked-cell force evaluation (no time step)",
                    "n": s.n},

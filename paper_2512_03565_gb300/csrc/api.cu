@@ -763,11 +763,11 @@ lj_status lj_get_cluster_lists(lj_ctx* h, int32_t* nbr, int32_t* nn, int32_t* ca
   if (nbr) {
     // packed entries (first slot << 3 | size - 1) back to cluster indices
     std::vector<uint32_t> packed(ncl * cap), cs(ncl + 1);
+    std::vector<int32_t> len(ncl);
     CK(cudaMemcpyAsync(packed.data(), c.vcl_nbr, ncl * cap * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaMemcpyAsync(cs.data(), c.cl_start, (ncl + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(len.data(), c.vcl_nn, ncl * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
-    std::vector<int32_t> len(ncl);
-    CK(cudaMemcpy(len.data(), c.vcl_nn, ncl * sizeof(int32_t), cudaMemcpyDeviceToHost));
     for (size_t I = 0; I < ncl; ++I)
       for (size_t k = 0; k < cap; ++k) {
         if ((int32_t)k >= len[I]) {
