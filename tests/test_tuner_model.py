@@ -20,6 +20,14 @@ def test_targets_are_relative_log_times():
     np.testing.assert_array_equal(M, [[1, 1, 0, 1], [1, 1, 1, 1]])
 
 
+def test_candidates_are_the_configurations_near_some_best():
+    # config 0 best in row 0; config 1 within 25 % in row 1; config 2 never within 25 %;
+    # config 3 best in row 1 but missing (NaN) in row 0
+    T = np.array([[1.0, 1.5, 2.0, np.nan], [2.0, 1.2, 3.0, 1.0]])
+    np.testing.assert_array_equal(tuner.candidates(T), [True, True, False, True])
+    np.testing.assert_array_equal(tuner.candidates(T, near=1.1), [True, False, False, True])
+
+
 def test_committed_model_ranks_its_training_rows():
     import os
     path = os.path.join(os.path.dirname(tuner.MODEL_PATH), "tuner_data.npz")
