@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--out", default=None, help="also append the JSON line to this file")
+    ap.add_argument("--oracle-baselines", action="store_true",
+                    help="time the CPU oracle on the host cores on every workload it serves as a baseline for, "
+                         "print one JSON line and exit (several minutes)")
     return ap.parse_args()
 
 
@@ -386,8 +389,57 @@ def run_ours(args, ws, rank, local, pg):
     return 0
 
 
+def run_oracle_baselines():
+    """The FP64 oracle on the host cores, as the reported CPU baselines:
+    - 1,000-particle uniform case: brute force and linked cells, one evaluation each;
+    - 1,048,576-particle fluid: linked cells (one evaluation, and a 100-step
+      velocity-Verlet run), and one brute-force evaluation as validation;
+    - 256-box batch: one linked-cell evaluation of every box, one after another.
+    Rates are in-cutoff (unique) pair evaluations per second."""
+    import oracle
+    from paper_2512_03565_gb300 import workloads as W
+    oracle.build()
+    out = {"kind": "oracle", "cores": oracle.num_threads(), "unit": "pairs/s"}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return r, time.perf_counter() - t0
+
+    s1 = W.config1()
+    (F1b, _, _, n1), t = timed(lambda: oracle.forces_bruteforce(s1.pos, s1.L, s1.rc))
+    out["uniform_1000_bruteforce"] = {"s": t, "pairs": int(n1), "rate": n1 / t}
+    (F1c, _, _, n1c), t = timed(lambda: oracle.forces_cells(s1.pos, s1.L, s1.rc))
+    out["uniform_1000_cells"] = {"s": t, "pairs": int(n1c), "rate": n1c / t,
+                                 "max_dF_over_rms_vs_bruteforce": float(
+                                     np.abs(F1c - F1b).max() / np.sqrt((F1b ** 2).sum(0).mean()))}
+    s2 = W.config2()
+    (F2c, _, _, n2), t = timed(lambda: oracle.forces_cells(s2.pos, s2.L, s2.rc))
+    out["fluid_1M_cells_one_eval"] = {"s": t, "pairs": int(n2), "rate": n2 / t}
+    (F2b, _, _, n2b), t = timed(lambda: oracle.forces_bruteforce(s2.pos, s2.L, s2.rc))
+    out["fluid_1M_bruteforce_one_eval"] = {"s": t, "pairs": int(n2b), "rate": n2b / t,
+                                           "max_dF_over_rms_cells_vs_bruteforce": float(
+                                               np.abs(F2c - F2b).max() / np.sqrt((F2b ** 2).sum(0).mean()))}
+    _, t = timed(lambda: oracle.vv_run(s2.pos, s2.vel, s2.L, s2.rc, 1.0, 0.002, 100, use_cells=True, forces=F2c))
+    out["fluid_1M_cells_100_steps"] = {"s": t, "steps": 100, "rate": 100 * n2 / t,
+                                       "note": "pair count of the first evaluation times 100"}
+    boxes = W.config5(256)
+    t_tot, p_tot = 0.0, 0
+    for b in boxes:
+        (_, _, _, nb), t = timed(lambda: oracle.forces_cells(b.pos, b.L, b.rc) if int(b.L // b.rc) >= 3
+                                 else oracle.forces_bruteforce(b.pos, b.L, b.rc))
+        t_tot += t
+        p_tot += nb
+    out["batch_256_boxes_one_eval_each"] = {"s": t_tot, "pairs": int(p_tot), "rate": p_tot / t_tot,
+                                            "particles": int(sum(b.n for b in boxes))}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.oracle_baselines:
+        return run_oracle_baselines()
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local, pg = dist_setup(args)
