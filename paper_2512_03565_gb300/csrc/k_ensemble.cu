@@ -275,13 +275,21 @@ __device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __r
       const uint4 pi = pos[i];
       const int m = min(A.nnbr[i], A.cap);
       const int32_t* row = A.nbr + i * A.cap;
-      for (int k0 = sub; k0 < m; k0 += W * 4) {
-        int jc[4];
+      // the next batch's entries are loaded while this batch's pairs are
+      // computed, as in the single-box list kernel
+      int jc[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) jc[t] = (k0 + t * W < m) ? __ldcs(row + k0 + t * W) : (int)i;
+      for (int t = 0; t < 4; ++t) jc[t] = (sub + t * W < m) ? __ldcs(row + sub + t * W) : (int)i;
+      for (int k0 = sub; k0 < m; k0 += W * 4) {
         uint4 pj[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) pj[t] = __ldg(pos + jc[t]);
+        int jn[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int k = k0 + W * 4 + t * W;
+          jn[t] = (k < m) ? __ldcs(row + k) : (int)i;
+        }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           float af, bf, cf;
@@ -291,6 +299,8 @@ __device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __r
           ay += fac * bf;
           az += fac * cf;
         }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) jc[t] = jn[t];
       }
     }
 #pragma unroll
