@@ -301,7 +301,9 @@ lj_status lj_get_state(lj_ctx* ctx, uint32_t* pos_fp, double* vel, int32_t on_de
 
 /* The pair set of a container, as original-index pairs (i < j) sorted
  * lexicographically: LJ_LC = pairs within r_c found by the linked-cell scan;
- * LJ_VL = the entries of the Verlet lists (pairs within r_c + skin).  With
+ * LJ_VL = the entries of the Verlet lists (pairs within r_c + skin);
+ * LJ_VCL = the member pairs of the listed cluster pairs that lie within
+ * r_c + skin (exact integer test), so equal to the LJ_VL set.  With
  * ij == NULL only *n_pairs is set (size query); otherwise ij must hold
  * 2 * (*n_pairs) int32 on the host. */
 lj_status lj_get_pairs(lj_ctx* ctx, int32_t container, int64_t* n_pairs, int32_t* ij);

@@ -950,6 +950,37 @@ lj_status lj_get_pairs(lj_ctx* h, int32_t container, int64_t* n_pairs, int32_t* 
       }
     *n_pairs = (int64_t)pairs.size();
     if (!ij) return LJ_OK;
+  } else if (container == LJ_VCL) {
+    if (!c.vcl_valid || c.binned_for != LJ_VCL) return fail(c, LJ_ERR_STATE, "no cluster list built");
+    const size_t n = (size_t)c.n, ncl = (size_t)c.vcl_ncl, cap = (size_t)c.vcl_cap;
+    std::vector<uint32_t> nbr(ncl * cap), cs(ncl + 1);
+    std::vector<int32_t> nn(ncl);
+    std::vector<uint4> pos(n);
+    CK(cudaMemcpyAsync(nbr.data(), c.vcl_nbr, ncl * cap * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(nn.data(), c.vcl_nn, ncl * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(cs.data(), c.cl_start, (ncl + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(pos.data(), c.pos, n * sizeof(uint4), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    for (size_t I = 0; I < ncl; ++I)
+      for (int k = 0; k < std::min(nn[I], (int32_t)cap); ++k) {
+        const uint32_t e = nbr[I * cap + k], jb = e >> 3, je = jb + (e & 7u) + 1u;
+        for (uint32_t a = cs[I]; a < cs[I + 1]; ++a)
+          for (uint32_t b = jb; b < je; ++b) {
+            const uint4 p = pos[a], q = pos[b];
+            const int dx = (int)(q.x - p.x), dy = (int)(q.y - p.y), dz = (int)(q.z - p.z);
+            const uint64_t R2 = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                                (uint64_t)((int64_t)dz * dz);
+            if (R2 == 0 || R2 > c.Rl2) continue;
+            const int32_t oa = (int32_t)p.w, ob = (int32_t)q.w;
+            if (c.vcl_half || oa < ob) pairs.emplace_back(std::min(oa, ob), std::max(oa, ob));
+          }
+      }
+    if (c.vcl_half) {  // the base cluster's own pairs appear twice in its self entry
+      std::sort(pairs.begin(), pairs.end());
+      pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+    }
+    *n_pairs = (int64_t)pairs.size();
+    if (!ij) return LJ_OK;
   } else {
     return fail(c, LJ_ERR_ARG, "unknown container");
   }

@@ -54,7 +54,10 @@ def test_cluster_order_and_lists_bit_exact(lj, M, half):
         perm, _, nt = d.cells()
         cs, nt2 = d.clusters()
         lists = d.cluster_lists()
+        vcl_pairs = d.pairs(lj.LJ_VCL)
         d.close()
+        # the member pairs within r_l of the listed cluster pairs are exactly the brute-force r_l pairs
+        assert np.array_equal(vcl_pairs, oracle.pairs_bruteforce(pos, L, rc + skin)), name
         perm_ref, cs_ref, lists_ref = oracle.vcl_lists(pos, L, rc + skin, M, half)
         assert nt == nt2 == oracle.vcl_ntower(pos.shape[1], M), name
         assert np.array_equal(perm, perm_ref), name
