@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-FLOPS_PER_PAIR = {0: 23, 1: 26, 2: 26}   # useful flops per unique pair by Newton-3 mode
+FLOPS_PER_PAIR = {0: 23, 1: 26, 2: 26, 3: 26}   # useful flops per unique pair by Newton-3 mode
 WORKLOAD = ("homogeneous LJ fluid, 1,048,576 particles, density 0.75 (L=111.82), rc 2.5, skin 0.3 "
             "(Verlet rebuild every 10 steps), T=1.0 Maxwell-Boltzmann, velocity Verlet dt=0.002, "
             "FP32 pair math with FP64 accumulation")
