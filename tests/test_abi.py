@@ -114,3 +114,14 @@ def test_energy_counter_absent_is_a_status_not_a_crash():
     with pytest.raises(lj.LJError) as e:
         lj.energy_read()
     assert e.value.status in (lj.LJ_ERR_STATE, lj.LJ_ERR_CUDA)
+
+
+def test_bench_tables_cover_every_configuration(lj):
+    """bench.py's per-mode figures (flops per pair) exist for every Newton-3 mode of the configuration list."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_module", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert {c.newton3 for c in lj.configs()} <= set(bench.FLOPS_PER_PAIR)
