@@ -129,3 +129,40 @@ def test_bench_fluid_full_size_sampled(lj, order):
     rms = np.sqrt((F_ref ** 2).sum(0).mean())
     assert np.abs(d.forces()[:, idx] - F_ref).max() / rms <= 1e-5
     d.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_boxes(lj, seed):
+    """Random box sizes and particle counts (1 to 9 towers per axis, a box
+    of 3 to 9 cutoffs, uniform and clumped placements): cluster lists equal
+    the oracle's and every cluster configuration's FP64 forces equal the
+    brute force."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(30, 2500))
+    L = float(rng.uniform(3.2, 9.0))
+    rc, skin = 1.0, float(rng.choice([0.0, 0.2, 0.4]))
+    if seed % 2:
+        pos = rng.integers(0, 2 ** 32, size=(3, n), dtype=np.uint64).astype(np.uint32)
+    else:  # clumps: most particles in a few small regions
+        centers = rng.integers(0, 2 ** 32, size=(3, 4), dtype=np.uint64)
+        pick = rng.integers(0, 4, size=n)
+        off = rng.integers(0, 2 ** 29, size=(3, n), dtype=np.uint64)
+        pos = ((centers[:, pick] + off) % 2 ** 32).astype(np.uint32)
+    F_ref, U_ref, _, np_ref = oracle.forces_bruteforce(pos, L, rc)
+    scale = max(np.sqrt((F_ref ** 2).sum(0).mean()), 1e-300)
+    d = lj.Domain(L, rc, skin, precision=lj.LJ_PREC_FP64)
+    d.set_particles(pos)
+    for M in (4, 6, 8):
+        for half in (0, 1):
+            d.build_clusters(M, half)
+            cs, _ = d.clusters()
+            lists = d.cluster_lists()
+            perm_ref, cs_ref, lists_ref = oracle.vcl_lists(pos, L, rc + skin, M, half)
+            assert np.array_equal(cs, cs_ref), (seed, M, half)
+            assert [sorted(x.tolist()) for x in lists] == [r.tolist() for r in lists_ref], (seed, M, half)
+    for cfg in [c for c in lj.configs() if c.container == lj.LJ_VCL]:
+        U, _ = d.compute_forces(cfg, energy=True)
+        assert np.abs(d.forces() - F_ref).max() <= 1e-12 * scale + 1e-300, (seed, lj.config_name(cfg))
+        assert abs(U - U_ref) <= 1e-12 * max(abs(U_ref), 1e-300), (seed, lj.config_name(cfg))
+        assert d.counters()[1] == np_ref
+    d.close()
