@@ -431,3 +431,33 @@ def test_state_errors(lj):
     with pytest.raises(lj.LJError, match="ARG"):
         small.compute_forces(lj.config(lj.LJ_VL, lj.LJ_ORD_VL_IPT))
     small.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_boxes_every_config(lj, seed):
+    """Random box sizes (3 to 9 cells per axis), particle counts and skins,
+    uniform or clumped: every configuration's FP64 forces, energy and pair
+    count equal the brute force."""
+    rng = np.random.default_rng(2000 + seed)
+    n = int(rng.integers(30, 2500))
+    L = float(rng.uniform(3.2, 9.5))
+    rc, skin = 1.0, float(rng.choice([0.0, 0.1, 0.4]))
+    if seed % 2:
+        pos = rng.integers(0, 2 ** 32, size=(3, n), dtype=np.uint64).astype(np.uint32)
+    else:
+        centers = rng.integers(0, 2 ** 32, size=(3, 3), dtype=np.uint64)
+        off = rng.integers(0, 2 ** 30, size=(3, n), dtype=np.uint64)
+        pos = ((centers[:, rng.integers(0, 3, size=n)] + off) % 2 ** 32).astype(np.uint32)
+    F_ref, U_ref, _, np_ref = oracle.forces_bruteforce(pos, L, rc)
+    scale = max(np.sqrt((F_ref ** 2).sum(0).mean()), 1e-300)
+    d = lj.Domain(L, rc, skin, precision=lj.LJ_PREC_FP64)
+    d.set_particles(pos)
+    nc_vl = int(np.floor(L / (rc + skin)))
+    for cfg in lj.configs():
+        if cfg.container == lj.LJ_VL and nc_vl < 3:
+            continue
+        U, _ = d.compute_forces(cfg, energy=True)
+        assert np.abs(d.forces() - F_ref).max() <= 1e-12 * scale + 1e-300, (seed, lj.config_name(cfg))
+        assert abs(U - U_ref) <= 1e-12 * max(abs(U_ref), 1e-300), (seed, lj.config_name(cfg))
+        assert d.counters()[1] == np_ref, (seed, lj.config_name(cfg))
+    d.close()
