@@ -97,6 +97,22 @@ __device__ __forceinline__ void bv_test(const float4& ci, const uint4& pi, float
   if (lane == q) my_cnt += __popc(mask);
 }
 
+// Membership of lane j in particle i's list (the coarse screen, and the
+// exact integer test in the band around r_l).
+template <bool HALF>
+__device__ __forceinline__ bool bv_in(const float4& ci, const uint4* s_iq, float jx, float jy, float jz,
+                                      const uint4& pj, int j, uint32_t i, uint64_t Rl2, float rl2p_lo,
+                                      float rl2p_hi) {
+  const float dx = jx - ci.x, dy = jy - ci.y, dz = jz - ci.z;  // exact (integers < 2^24)
+  const float r2p = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  bool in = (HALF ? j > (int)i : j != (int)i) && r2p <= rl2p_hi;
+  if (in && r2p >= rl2p_lo) {
+    const uint4 pi = *s_iq;
+    in = in_cut_exact(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), Rl2);
+  }
+  return in;
+}
+
 // The scan of one tile: particles first .. first + ni - 1 (ni <= 32), whose
 // positions and coarse coordinates this warp has put in s_i / s_c, against the
 // segments.  Chunks of 32 j's are packed across segment boundaries (each lane
@@ -121,17 +137,20 @@ __device__ __forceinline__ uint32_t bv_tile(const uint4* __restrict__ pos, const
     total += segs[s].e - segs[s].b;
   }
   if (!mixed) {
+    // Chunks of 64: each lane holds two j's (positions c0 + lane and c0 + 32 +
+    // lane of the packed neighbourhood), so that an i's ballots, its running
+    // count and its store address serve 64 tests.  The first 32 j's survivors
+    // are stored before the second 32's: the order is that of 32-wide chunks.
     int sl = 0;
     uint32_t off = lane;  // this lane's position within segment sl
-#pragma unroll 1
-    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+    auto load_j = [&](int& j, uint4& pj, float& jx, float& jy, float& jz) {
       while (sl < ns && off >= segs[sl].e - segs[sl].b) {
         off -= segs[sl].e - segs[sl].b;
         ++sl;
       }
-      int j = -1;
-      uint4 pj = make_uint4(0, 0, 0, 0);
-      float jx = -1e30f, jy = -1e30f, jz = -1e30f;
+      j = -1;
+      pj = make_uint4(0, 0, 0, 0);
+      jx = jy = jz = -1e30f;
       if (sl < ns) {
         const BSeg& sg = segs[sl];
         j = (int)(sg.b + off);
@@ -140,11 +159,41 @@ __device__ __forceinline__ uint32_t bv_tile(const uint4* __restrict__ pos, const
         jy = coarse_coord(pj.y) + sg.sy;
         jz = coarse_coord(pj.z) + sg.sz;
       }
-#pragma unroll 4
-      for (int q = 0; q < ni; ++q)
-        bv_test<HALF, COLMAJOR, false>(s_c[q], s_i[q], jx, jy, jz, pj, j, first + q, q, lane, lt, n,
-                                       cap, Rl2, rl2p_lo, rl2p_hi, nbr, my_cnt);
       off += 32;
+    };
+#pragma unroll 1
+    for (uint32_t c0 = 0; c0 < total; c0 += 64) {
+      int j0, j1;
+      uint4 p0, p1;
+      float x0, y0, z0, x1, y1, z1;
+      load_j(j0, p0, x0, y0, z0);
+      load_j(j1, p1, x1, y1, z1);
+#pragma unroll 2
+      for (int q = 0; q < ni; ++q) {
+        const float4 ci = s_c[q];
+        const uint32_t i = first + q;
+        const unsigned m0 = __ballot_sync(0xffffffffu, bv_in<HALF>(ci, s_i + q, x0, y0, z0, p0, j0, i, Rl2,
+                                                                      rl2p_lo, rl2p_hi));
+        const unsigned m1 = __ballot_sync(0xffffffffu, bv_in<HALF>(ci, s_i + q, x1, y1, z1, p1, j1, i, Rl2,
+                                                                      rl2p_lo, rl2p_hi));
+        const uint32_t base = __shfl_sync(0xffffffffu, my_cnt, q);
+        const uint32_t c0n = (uint32_t)__popc(m0);
+        if ((m0 >> lane) & 1u) {
+          const uint32_t k = base + __popc(m0 & lt);
+          if (k < (uint32_t)cap) {
+            if (COLMAJOR) nbr[(int64_t)k * n + i] = j0;
+            else nbr[(int64_t)i * cap + k] = j0;
+          }
+        }
+        if ((m1 >> lane) & 1u) {
+          const uint32_t k = base + c0n + __popc(m1 & lt);
+          if (k < (uint32_t)cap) {
+            if (COLMAJOR) nbr[(int64_t)k * n + i] = j1;
+            else nbr[(int64_t)i * cap + k] = j1;
+          }
+        }
+        if (lane == q) my_cnt += c0n + (uint32_t)__popc(m1);
+      }
     }
   } else {
 #pragma unroll 1
