@@ -137,10 +137,10 @@ __device__ __forceinline__ uint32_t bv_tile(const uint4* __restrict__ pos, const
     total += segs[s].e - segs[s].b;
   }
   if (!mixed) {
-    // Chunks of 64: each lane holds two j's (positions c0 + lane and c0 + 32 +
-    // lane of the packed neighbourhood), so that an i's ballots, its running
-    // count and its store address serve 64 tests.  The first 32 j's survivors
-    // are stored before the second 32's: the order is that of 32-wide chunks.
+    // Chunks of 32 JPL: each lane holds JPL j's (positions c0 + 32 u + lane of
+    // the packed neighbourhood), so that an i's running count and store
+    // address serve 32 JPL tests.  The u-th 32 j's survivors are stored before
+    // the (u+1)-th's: the order is that of 32-wide chunks.
     int sl = 0;
     uint32_t off = lane;  // this lane's position within segment sl
     auto load_j = [&](int& j, uint4& pj, float& jx, float& jy, float& jz) {
@@ -161,38 +161,36 @@ __device__ __forceinline__ uint32_t bv_tile(const uint4* __restrict__ pos, const
       }
       off += 32;
     };
+    constexpr int JPL = 4;  // j's per lane
 #pragma unroll 1
-    for (uint32_t c0 = 0; c0 < total; c0 += 64) {
-      int j0, j1;
-      uint4 p0, p1;
-      float x0, y0, z0, x1, y1, z1;
-      load_j(j0, p0, x0, y0, z0);
-      load_j(j1, p1, x1, y1, z1);
+    for (uint32_t c0 = 0; c0 < total; c0 += 32 * JPL) {
+      int jv[JPL];
+      uint4 pv[JPL];
+      float xv[JPL], yv[JPL], zv[JPL];
+#pragma unroll
+      for (int u = 0; u < JPL; ++u) load_j(jv[u], pv[u], xv[u], yv[u], zv[u]);
 #pragma unroll 2
       for (int q = 0; q < ni; ++q) {
         const float4 ci = s_c[q];
         const uint32_t i = first + q;
-        const unsigned m0 = __ballot_sync(0xffffffffu, bv_in<HALF>(ci, s_i + q, x0, y0, z0, p0, j0, i, Rl2,
-                                                                      rl2p_lo, rl2p_hi));
-        const unsigned m1 = __ballot_sync(0xffffffffu, bv_in<HALF>(ci, s_i + q, x1, y1, z1, p1, j1, i, Rl2,
-                                                                      rl2p_lo, rl2p_hi));
-        const uint32_t base = __shfl_sync(0xffffffffu, my_cnt, q);
-        const uint32_t c0n = (uint32_t)__popc(m0);
-        if ((m0 >> lane) & 1u) {
-          const uint32_t k = base + __popc(m0 & lt);
-          if (k < (uint32_t)cap) {
-            if (COLMAJOR) nbr[(int64_t)k * n + i] = j0;
-            else nbr[(int64_t)i * cap + k] = j0;
+        unsigned m[JPL];
+#pragma unroll
+        for (int u = 0; u < JPL; ++u)
+          m[u] = __ballot_sync(0xffffffffu, bv_in<HALF>(ci, s_i + q, xv[u], yv[u], zv[u], pv[u], jv[u], i, Rl2,
+                                                          rl2p_lo, rl2p_hi));
+        uint32_t k = __shfl_sync(0xffffffffu, my_cnt, q);
+#pragma unroll
+        for (int u = 0; u < JPL; ++u) {
+          if ((m[u] >> lane) & 1u) {
+            const uint32_t kk = k + __popc(m[u] & lt);
+            if (kk < (uint32_t)cap) {
+              if (COLMAJOR) nbr[(int64_t)kk * n + i] = jv[u];
+              else nbr[(int64_t)i * cap + kk] = jv[u];
+            }
           }
+          k += (uint32_t)__popc(m[u]);
         }
-        if ((m1 >> lane) & 1u) {
-          const uint32_t k = base + c0n + __popc(m1 & lt);
-          if (k < (uint32_t)cap) {
-            if (COLMAJOR) nbr[(int64_t)k * n + i] = j1;
-            else nbr[(int64_t)i * cap + k] = j1;
-          }
-        }
-        if (lane == q) my_cnt += c0n + (uint32_t)__popc(m1);
+        if (lane == q) my_cnt = k;
       }
     }
   } else {
