@@ -46,8 +46,10 @@ __global__ void __launch_bounds__(256) k_build_verlet(const uint4* __restrict__ 
                                                      rl2p_lo, rl2p_hi, nbr);
     if (lane < ni) {
       nnbr[tile.x + lane] = (int32_t)my_cnt;
-      if (my_cnt > (uint32_t)cap) atomicOr(status, ST_CAPACITY);
-      atomicMax(maxlen, my_cnt);
+      if (my_cnt > (uint32_t)cap) {  // only an overflow needs the longest length (for the regrowth)
+        atomicOr(status, ST_CAPACITY);
+        atomicMax(maxlen, my_cnt);
+      }
     }
     __syncwarp();
   }

@@ -397,7 +397,7 @@ struct Ctx {
   unsigned long long* rev_key2 = nullptr;  // cap * n
   size_t rev_cap = 0;             // entries allocated in rev_slot / rev_key
   bool rev_valid = false;
-  uint32_t* maxlen = nullptr;     // device: longest list of the last build
+  uint32_t* maxlen = nullptr;     // device: longest list of the last build, when it overflowed the capacity
 
   // accumulators and status
   double* ev = nullptr;    // 2 doubles, then the pair counter (one allocation, cleared by one memset)
