@@ -375,17 +375,45 @@ __global__ void k_row_tiles(const uint32_t* __restrict__ cs, int nc, int Tsigned
   if (!WRITE) row_cnt[r] = k;
 }
 
+// Single-cell tiles (T < 0), one thread per cell: the same tiles as the row
+// scan above, in the same (cell) order, from per-cell counts and their scan.
+template <bool WRITE>
+__global__ void k_cell_tiles(const uint32_t* __restrict__ cs, int64_t ncell, int nc, uint32_t T,
+                             uint32_t* __restrict__ cnt_off, uint4* __restrict__ tiles) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const uint32_t b = cs[c], e = cs[c + 1];
+  if (!WRITE) {
+    cnt_off[c] = (e - b + T - 1u) / T;
+    return;
+  }
+  const uint32_t row = (uint32_t)(c / nc), cx = (uint32_t)(c % nc);
+  uint32_t k = cnt_off[c];
+  for (uint32_t p = b; p < e; p += T) tiles[k++] = make_uint4(p, min(p + T, e), row, cx | (cx << 16));
+}
+
 cudaError_t build_tiles(Ctx& c, int T) {
   if (c.tiles_T == T && c.tiles_gen == c.bin_gen && c.tiles_for_nc == c.binned_nc) return cudaSuccess;
   const int nc = c.binned_nc;
-  const int64_t nrow = (int64_t)nc * nc;
+  const int64_t nrow = (int64_t)nc * nc, ncell = nrow * nc;
   cudaError_t e;
-  if ((e = grow(c.row_tiles, c.row_tiles_cap, (size_t)nrow + 1)) != cudaSuccess) return e;
   // worst case: one tile per particle plus one per row
   if ((e = grow(c.tiles, c.tiles_cap, (size_t)(c.n + nrow + 1))) != cudaSuccess) return e;
-  k_row_tiles<false><<<nblk(nrow, 128), 128, 0, c.stream>>>(c.cell_start, nc, T, c.row_tiles, c.tiles);
-  if ((e = excl_scan_u32(c, c.row_tiles, c.row_tiles, nrow)) != cudaSuccess) return e;
-  k_row_tiles<true><<<nblk(nrow, 128), 128, 0, c.stream>>>(c.cell_start, nc, T, c.row_tiles, c.tiles);
+  if (T < 0) {
+    if ((e = grow(c.row_tiles, c.row_tiles_cap, (size_t)ncell + 1)) != cudaSuccess) return e;
+    k_cell_tiles<false><<<nblk(ncell, 256), 256, 0, c.stream>>>(c.cell_start, ncell, nc, (uint32_t)(-T),
+                                                                c.row_tiles, c.tiles);
+    if ((e = excl_scan_u32(c, c.row_tiles, c.row_tiles, ncell)) != cudaSuccess) return e;
+    k_cell_tiles<true><<<nblk(ncell, 256), 256, 0, c.stream>>>(c.cell_start, ncell, nc, (uint32_t)(-T),
+                                                               c.row_tiles, c.tiles);
+    c.ntiles_dev = c.row_tiles + ncell;
+  } else {
+    if ((e = grow(c.row_tiles, c.row_tiles_cap, (size_t)nrow + 1)) != cudaSuccess) return e;
+    k_row_tiles<false><<<nblk(nrow, 128), 128, 0, c.stream>>>(c.cell_start, nc, T, c.row_tiles, c.tiles);
+    if ((e = excl_scan_u32(c, c.row_tiles, c.row_tiles, nrow)) != cudaSuccess) return e;
+    k_row_tiles<true><<<nblk(nrow, 128), 128, 0, c.stream>>>(c.cell_start, nc, T, c.row_tiles, c.tiles);
+    c.ntiles_dev = c.row_tiles + nrow;
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   c.tiles_T = T;
   c.tiles_gen = c.bin_gen;

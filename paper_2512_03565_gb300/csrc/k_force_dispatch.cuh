@@ -18,14 +18,14 @@ inline unsigned grid_for(int64_t threads, int tpb, int per_sm) {
 
 template <typename R, bool N3, bool EV, bool BWD>
 cudaError_t lc_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
-  LCArgs A{c.pos, c.cell_start, c.tiles, c.row_tiles + (size_t)c.binned_nc * c.binned_nc, c.tile_ctr};
+  LCArgs A{c.pos, c.cell_start, c.tiles, c.ntiles_dev, c.tile_ctr};
   cudaError_t e;
   const int64_t n = c.n;
   auto prep = [&](int T) -> cudaError_t {
     cudaError_t r = build_tiles(c, T);
     if (r != cudaSuccess) return r;
     A.tiles = c.tiles;
-    A.ntiles = c.row_tiles + (size_t)c.binned_nc * c.binned_nc;
+    A.ntiles = c.ntiles_dev;
     return cudaMemsetAsync(c.tile_ctr, 0, sizeof(uint32_t), c.stream);
   };
   switch (cfg.order) {

@@ -105,7 +105,7 @@ cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen
   cudaError_t e = build_tiles(c, -32);  // single-cell tiles: exact 27-cell candidate sets
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c.tile_ctr, 0, sizeof(uint32_t), c.stream)) != cudaSuccess) return e;
-  const uint32_t* ntiles = c.row_tiles + (size_t)c.binned_nc * c.binned_nc;
+  const uint32_t* ntiles = c.ntiles_dev;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8);
   auto k = half ? (colmajor ? k_build_verlet<true, true> : k_build_verlet<true, false>)
                 : (colmajor ? k_build_verlet<false, true> : k_build_verlet<false, false>);

@@ -344,7 +344,8 @@ struct Ctx {
   uint4* tiles = nullptr;  // (begin, end, row, cx_first | cx_last << 16)
   size_t tiles_cap = 0;
   int ntiles = 0;
-  uint32_t* row_tiles = nullptr;  // per row tile counts / offsets
+  uint32_t* row_tiles = nullptr;  // per row (per cell for single-cell tiles) tile counts / offsets
+  const uint32_t* ntiles_dev = nullptr;  // device count of the current tiles
   size_t row_tiles_cap = 0;
   uint64_t bin_gen = 0;    // increments at every binning
   uint32_t* tile_ctr = nullptr;  // device work counter of the tile kernels
