@@ -511,3 +511,48 @@ def test_features_of_hand_built_configuration(orc):
     assert f[13] == pytest.approx(blocks.std() / blocks.mean())
     assert f[14] == pytest.approx(1.0)
     assert f[15] == pytest.approx((38 / 8) * (4 / 3 * math.pi * 2.8 ** 3) / 2.5 ** 3)
+
+
+# --- linked-cell half shells (readings R5 and R20) ------------------------------
+
+def _half_shell_pairs(pos, L, r, backward):
+    """Pairs found by visiting, for every particle, the forward (R5) or backward
+    (R20) half shell of cells: own cell with j after (before) i in cell order,
+    and the 13 cells ahead (behind) of it; written from the readings, in plain
+    Python, on the oracle's cell order."""
+    import oracle as orc
+    n = pos.shape[1]
+    nc = orc.ncells(L, r)
+    perm, cs = orc.bin_cells(pos, nc)
+    slot = np.empty(n, dtype=np.int64)
+    slot[perm] = np.arange(n)
+    R2max = orc.cut2_int(L, r)
+    sgn = -1 if backward else 1
+    # the 13 forward neighbour offsets (dz, dy, dx): (0,0,+1), (0,+1,*), (+1,*,*)
+    fwd = [(0, 0, 1)] + [(0, 1, dx) for dx in (-1, 0, 1)] + [(1, dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    out = []
+    for i in range(n):
+        ci = [int((int(pos[a, i]) * nc) >> 32) for a in range(3)]
+        c_lin = (ci[2] * nc + ci[1]) * nc + ci[0]
+        cand = [j for j in perm[cs[c_lin]:cs[c_lin + 1]] if sgn * (slot[j] - slot[i]) > 0]
+        for dz, dy, dx in fwd:
+            z, y, x = (ci[2] + sgn * dz) % nc, (ci[1] + sgn * dy) % nc, (ci[0] + sgn * dx) % nc
+            c2 = (z * nc + y) * nc + x
+            cand += list(perm[cs[c2]:cs[c2 + 1]])
+        for j in cand:
+            R2 = orc.r2_int(pos[:, i], pos[:, j])
+            if 0 < R2 <= R2max:
+                out.append((min(i, int(j)), max(i, int(j))))
+    return out
+
+
+@pytest.mark.parametrize("backward", [False, True])
+def test_half_shells_cover_every_pair_once(orc, backward):
+    """Both half shells of the linked-cell Newton-3 orders find every pair of the
+    brute force exactly once (the backward one is the forward one with the
+    roles of the two cells of every pair swapped)."""
+    for name, L, pos in tiny_cases():
+        got = _half_shell_pairs(pos, L, 1.0, backward)
+        assert len(got) == len(set(got)), name                      # no pair twice
+        bf = {tuple(int(v) for v in p) for p in orc.pairs_bruteforce(pos, L, 1.0)}
+        assert set(got) == bf, name
