@@ -57,7 +57,8 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        # LJ_ORACLE_LIB: an alternative build of lj_oracle.c (the sanitizer test)
+        lib = C.CDLL(os.environ.get("LJ_ORACLE_LIB") or build())
         i64, f64, u32, u64, i32 = C.c_int64, C.c_double, C.c_uint32, C.c_uint64, C.c_int
         vp = C.c_void_p
         sig = {
