@@ -15,12 +15,17 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+# LJGB_CHECKS=1: a separate build whose kernels check every index they read
+# from data (list entries, segments, cluster entries, permutation slots) and
+# set a status bit instead of making the access (LJ_ERR_CUDA "device index
+# check failed" at the next status read).
+CHECKS = os.environ.get("LJGB_CHECKS", "0") not in ("", "0")
+OUT = os.path.join(HERE, "_build_checks" if CHECKS else "_build")
 LIB = os.path.join(OUT, "libljgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr"]
+         "--expt-relaxed-constexpr"] + (["-DLJGB_CHECKS=1"] if CHECKS else [])
 
 
 def _headers_mtime() -> float:

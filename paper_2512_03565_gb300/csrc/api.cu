@@ -697,7 +697,8 @@ lj_status lj_update_positions(lj_ctx* h, const double* pos, int32_t on_device) {
   const double hs = 0.5 * c.skin * 4294967296.0 / c.L;
   const uint64_t d2max = hs * hs >= 1.8e19 ? ~0ull : (uint64_t)(hs * hs);
   if (check) *reinterpret_cast<volatile uint32_t*>(c.skin_host) = 0u;
-  CK(launch_update_pos(c.pos, c.inv, dpos, c.n, c.L, check ? c.x_build : nullptr, d2max, c.skin_dev, c.stream));
+  CK(launch_update_pos(c.pos, c.inv, dpos, c.n, c.L, check ? c.x_build : nullptr, d2max, c.skin_dev, c.stream,
+                       c.status));
   if (check) CK(cudaEventRecord(c.drift_done, c.stream));
   c.skin_pending = check;
   c.launches += 1;
@@ -869,14 +870,14 @@ lj_status lj_get_forces(lj_ctx* h, double* dst, int32_t on_device) {
   CKS(need_particles(c));
   if (!c.forces_valid) return fail(c, LJ_ERR_STATE, "no forces computed");
   if (on_device) {
-    CK(launch_from_slots(c.inv, c.frc, c.n, dst, c.stream));
+    CK(launch_from_slots(c.inv, c.frc, c.n, dst, c.stream, c.status));
     return LJ_OK;
   }
   if (double* mapped = (double*)host_mapped(dst)) {  // written by the kernel across the host link
-    CK(launch_from_slots(c.inv, c.frc, c.n, mapped, c.stream));
+    CK(launch_from_slots(c.inv, c.frc, c.n, mapped, c.stream, c.status));
     return take_status(c);
   }
-  CK(launch_from_slots(c.inv, c.frc, c.n, c.frc_alt, c.stream));
+  CK(launch_from_slots(c.inv, c.frc, c.n, c.frc_alt, c.stream, c.status));
   CK(cudaMemcpyAsync(dst, c.frc_alt, 3 * (size_t)c.n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   return take_status(c);
 }
@@ -889,19 +890,19 @@ lj_status lj_get_state(lj_ctx* h, uint32_t* pos_fp, double* vel, int32_t on_devi
   const size_t n = (size_t)c.n;
   if (pos_fp) {
     if (on_device) {
-      CK(launch_pos_to_original(c.pos, c.n, pos_fp, c.stream));
+      CK(launch_pos_to_original(c.pos, c.n, pos_fp, c.stream, c.status));
     } else {
       uint32_t* tmp = (uint32_t*)c.vel_alt;  // 3n doubles of scratch hold 3n uint32
-      CK(launch_pos_to_original(c.pos, c.n, tmp, c.stream));
+      CK(launch_pos_to_original(c.pos, c.n, tmp, c.stream, c.status));
       CK(cudaMemcpyAsync(pos_fp, tmp, 3 * n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
       CK(cudaStreamSynchronize(c.stream));
     }
   }
   if (vel) {
     if (on_device) {
-      CK(launch_to_original(c.pos, c.vel, c.n, vel, c.stream));
+      CK(launch_to_original(c.pos, c.vel, c.n, vel, c.stream, c.status));
     } else {
-      CK(launch_to_original(c.pos, c.vel, c.n, c.vel_alt, c.stream));
+      CK(launch_to_original(c.pos, c.vel, c.n, c.vel_alt, c.stream, c.status));
       CK(cudaMemcpyAsync(vel, c.vel_alt, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
       CK(cudaStreamSynchronize(c.stream));
     }

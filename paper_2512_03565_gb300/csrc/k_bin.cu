@@ -48,10 +48,11 @@ __global__ void k_quantize(const double* __restrict__ pos, int64_t n, double L, 
 // word skin_flag.
 __global__ void k_update_pos(uint4* __restrict__ pos, const uint32_t* __restrict__ inv, const double* __restrict__ x,
                              int64_t n, double L, const uint32_t* __restrict__ xb, uint64_t disp2_max,
-                             uint32_t* skin_flag) {
+                             uint32_t* skin_flag, uint32_t* status) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
   const uint32_t s = inv[o];
+  if (!LJ_IDX_OK(s < (uint64_t)n, status)) return;
   const uint4 p = make_uint4(quantize_coord(x[o], L), quantize_coord(x[n + o], L), quantize_coord(x[2 * n + o], L),
                              (uint32_t)o);
   pos[s] = p;
@@ -86,8 +87,9 @@ cudaError_t launch_quantize(const double* pos, int64_t n, double L, const double
 }
 
 cudaError_t launch_update_pos(uint4* pos, const uint32_t* inv, const double* x, int64_t n, double L,
-                              const uint32_t* xb, uint64_t disp2_max, uint32_t* skin_flag, cudaStream_t s) {
-  k_update_pos<<<nblk(n, 256), 256, 0, s>>>(pos, inv, x, n, L, xb, disp2_max, skin_flag);
+                              const uint32_t* xb, uint64_t disp2_max, uint32_t* skin_flag, cudaStream_t s,
+                              uint32_t* status) {
+  k_update_pos<<<nblk(n, 256), 256, 0, s>>>(pos, inv, x, n, L, xb, disp2_max, skin_flag, status);
   return cudaGetLastError();
 }
 
@@ -278,13 +280,15 @@ cudaError_t sort_segments(Ctx& c, const uint32_t* starts, int64_t nseg, unsigned
 
 __global__ void k_permute(const unsigned long long* __restrict__ key, int64_t n, const uint4* __restrict__ pos,
                           const double* __restrict__ vel, const double* __restrict__ frc, uint4* __restrict__ pos2,
-                          double* __restrict__ vel2, double* __restrict__ frc2, uint32_t* __restrict__ inv) {
+                          double* __restrict__ vel2, double* __restrict__ frc2, uint32_t* __restrict__ inv,
+                          uint32_t* status) {
   int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= n) return;
   const uint32_t s = (uint32_t)(key[d] & 0xffffffffull);
+  if (!LJ_IDX_OK(s < (uint64_t)n, status)) return;
   const uint4 p = pos[s];
   pos2[d] = p;
-  inv[p.w] = (uint32_t)d;  // original index -> new slot
+  if (LJ_IDX_OK(p.w < (uint64_t)n, status)) inv[p.w] = (uint32_t)d;  // original index -> new slot
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     vel2[a * n + d] = vel[a * n + s];
@@ -316,7 +320,7 @@ cudaError_t bin_cells(Ctx& c, int nc) {
   unsigned long long* key2 = c.key + n;
   if ((e = sort_segments(c, c.cell_start, ncell, c.key, key2)) != cudaSuccess) return e;
   k_permute<<<nblk(n, 256), 256, 0, c.stream>>>(key2, n, c.pos, c.vel, c.frc, c.pos_alt, c.vel_alt, c.frc_alt,
-                                                 c.inv);
+                                                 c.inv, c.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   std::swap(c.pos, c.pos_alt);
   std::swap(c.vel, c.vel_alt);

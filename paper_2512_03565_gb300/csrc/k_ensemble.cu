@@ -208,6 +208,7 @@ __device__ __forceinline__ void ens_forces(const EnsArgs& A, const uint4* __rest
         const int nc = B.nc;
         const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
         ns = make_segments<false>(cs + B.cell_off, nc, cz * nc + cy, cx, cx, (uint32_t)i, (uint32_t)i + 1u, segs);
+        check_segs(segs, ns, (uint32_t)A.ntot, A.status);
       } else {
         segs[0] = {(uint32_t)B.off, (uint32_t)(B.off + B.n), 0};
         ns = 1;
@@ -279,7 +280,10 @@ __device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __r
       // computed, as in the single-box list kernel
       int jc[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) jc[t] = (sub + t * W < m) ? __ldcs(row + sub + t * W) : (int)i;
+      for (int t = 0; t < 4; ++t) {
+        jc[t] = (sub + t * W < m) ? __ldcs(row + sub + t * W) : (int)i;
+        if (!LJ_IDX_OK((uint64_t)(uint32_t)jc[t] < (uint64_t)A.ntot, A.status)) jc[t] = (int)i;
+      }
       for (int k0 = sub; k0 < m; k0 += W * 4) {
         uint4 pj[4];
 #pragma unroll
@@ -289,6 +293,7 @@ __device__ __forceinline__ void ens_forces_vl(const EnsArgs& A, const uint4* __r
         for (int t = 0; t < 4; ++t) {
           const int k = k0 + W * 4 + t * W;
           jn[t] = (k < m) ? __ldcs(row + k) : (int)i;
+          if (!LJ_IDX_OK((uint64_t)(uint32_t)jn[t] < (uint64_t)A.ntot, A.status)) jn[t] = (int)i;
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -843,6 +848,11 @@ lj_status lj_ensemble_run(lj_ens* h, double dt, int32_t nsteps, int32_t use_grap
   if (st & ST_NONFINITE) {
     E.err = "non-finite force";
     return LJ_ERR_NONFINITE;
+  }
+  if (st & ST_OOB) {
+    E.err = "device index check failed";
+    E.forces_valid = false;
+    return LJ_ERR_CUDA;
   }
   if (st & ST_CAPACITY) {
     E.err = "a Verlet list outgrew the capacity (lj_ensemble_set_lists with a larger cap); the run stopped mid-step";

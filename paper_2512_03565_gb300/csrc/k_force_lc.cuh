@@ -121,6 +121,20 @@ __device__ __forceinline__ int make_segments(const uint32_t* __restrict__ cs, in
   return ns;
 }
 
+// Checks build: a segment outside [0, n] (a corrupt cell start) is emptied
+// and reported; in the default build this does nothing.
+__device__ __forceinline__ void check_segs(Seg* segs, int ns, uint32_t n, uint32_t* status) {
+#ifdef LJGB_CHECKS
+  for (int s = 0; s < ns; ++s)
+    if (!LJ_IDX_OK(segs[s].b <= segs[s].e && segs[s].e <= n, status)) segs[s].b = segs[s].e = 0u;
+#else
+  (void)segs;
+  (void)ns;
+  (void)n;
+  (void)status;
+#endif
+}
+
 template <bool BWD = false>
 __device__ __forceinline__ bool seg_ok(int kind, uint32_t j, uint32_t i, uint32_t cxi, int nc) {
   if (kind == 0) return true;
@@ -180,6 +194,7 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
     R eu = 0, ew = 0;
     Seg segs[18];
     const int ns = make_segments<N3, BWD>(A.cs, nc, (int)tile.z, cf, cl, tile.x, tile.y, segs);
+    check_segs(segs, ns, (uint32_t)P.n, out.status);
 #pragma unroll 1
     for (int s = 0; s < ns; ++s) {
       const Seg sg = segs[s];
@@ -333,6 +348,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
     Seg segs[18];
     const int ns = make_segments<N3, BWD>(A.cs, nc, (int)tile.z, cf, cl, tile.x, tile.y, segs);
+    check_segs(segs, ns, (uint32_t)P.n, out.status);
     // flatten (segment, offset) into chunks; issue chunk c+1 while computing c
     int s_cur = 0;
     uint32_t o_cur = 0;
@@ -462,6 +478,7 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
     Seg segs[18];
     const int ns = make_segments<N3, BWD>(A.cs, nc, (int)tile.z, cf, cl, tile.x, tile.y, segs);
+    check_segs(segs, ns, (uint32_t)P.n, out.status);
 #pragma unroll 1
     for (int s = 0; s < ns; ++s) {
       const Seg sg = segs[s];
@@ -542,6 +559,7 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
     const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
     Seg segs[18];
     int ns = vi ? make_segments<N3, BWD>(cs, nc, cz * nc + cy, cx, cx, ii, ii, segs) : 0;
+    check_segs(segs, ns, (uint32_t)P.n, out.status);
     const int nsmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)ns);
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
 #pragma unroll 1

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(256) k_vcl_tile(LJParams P, VclArgs A, ForceOu
     for (uint32_t q0 = 0; q0 < slots; q0 += JP) {
       const uint32_t q = q0 + (uint32_t)js;
       const bool vq = act && q < slots;
-      const uint32_t ent = vq ? row[q / M] : ib << 3;  // a slot past the list reads the base cluster
+      uint32_t ent = vq ? row[q / M] : ib << 3;  // a slot past the list reads the base cluster
+      if (!LJ_IDX_OK((ent >> 3) + (ent & 7u) < (uint32_t)P.n, out.status)) ent = ib << 3;
       const uint32_t jb = ent >> 3, jj = q % M;
       const bool vj = vq && jj <= (ent & 7u);
       const uint32_t j = jb + jj;
@@ -162,7 +163,8 @@ __global__ void __launch_bounds__(256) k_vcl_jlane(LJParams P, VclArgs A, ForceO
     for (uint32_t q0 = 0; q0 < slots; q0 += 32) {
       const uint32_t q = q0 + (uint32_t)lane;
       const bool vq = q < slots;
-      const uint32_t ent = vq ? row[q / M] : ib << 3;  // a slot past the list reads the base cluster
+      uint32_t ent = vq ? row[q / M] : ib << 3;  // a slot past the list reads the base cluster
+      if (!LJ_IDX_OK((ent >> 3) + (ent & 7u) < (uint32_t)P.n, out.status)) ent = ib << 3;
       const uint32_t jb = ent >> 3, jj = q % M;
       const bool vj = vq && jj <= (ent & 7u);
       const uint32_t j = jb + jj;

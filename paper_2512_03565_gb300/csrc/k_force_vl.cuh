@@ -38,7 +38,8 @@ __device__ __forceinline__ int vl_entry(const VLArgs& A, int64_t e, int64_t i, i
     j -= (j >= n) ? n : 0;
     return (int)j;
   }
-  return __ldcs(A.nbr + e);
+  const int j = __ldcs(A.nbr + e);
+  return LJ_IDX_OK((unsigned)j < (unsigned)n, A.status) ? j : (int)i;  // checks build: self, no pair
 }
 
 // Stores the FP64 force of particle i; a non-finite component sets
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, Forc
           j -= (j >= n) ? n : 0;
           return (int)j;
         }
-        return __ldcs(rp + off);
+        const int j = __ldcs(rp + off);
+        return LJ_IDX_OK((unsigned)j < (unsigned)n, A.status) ? j : (int)i;  // checks build: self, no pair
       };
       int jc[VL_BATCH];
 #pragma unroll

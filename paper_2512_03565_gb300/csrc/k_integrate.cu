@@ -70,19 +70,22 @@ cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, b
 
 // dst[a][orig(s)] = src[a][s]
 __global__ void k_to_original(const uint4* __restrict__ pos, const double* __restrict__ src, int64_t n,
-                              double* __restrict__ dst) {
+                              double* __restrict__ dst, uint32_t* status) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const uint32_t o = pos[s].w;
+  if (!LJ_IDX_OK(o < (uint64_t)n, status)) return;
   dst[o] = src[s];
   dst[n + o] = src[n + s];
   dst[2 * n + o] = src[2 * n + s];
 }
 
-__global__ void k_pos_to_original(const uint4* __restrict__ pos, int64_t n, uint32_t* __restrict__ dst) {
+__global__ void k_pos_to_original(const uint4* __restrict__ pos, int64_t n, uint32_t* __restrict__ dst,
+                                  uint32_t* status) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const uint4 p = pos[s];
+  if (!LJ_IDX_OK(p.w < (uint64_t)n, status)) return;
   dst[p.w] = p.x;
   dst[n + p.w] = p.y;
   dst[2 * n + p.w] = p.z;
@@ -91,27 +94,31 @@ __global__ void k_pos_to_original(const uint4* __restrict__ pos, int64_t n, uint
 // dst[a][o] = src[a][inv[o]]: writes in the caller's order (coalesced), so dst
 // may also be the caller's pinned host memory written across the host link.
 __global__ void k_from_slots(const uint32_t* __restrict__ inv, const double* __restrict__ src, int64_t n,
-                             double* __restrict__ dst) {
+                             double* __restrict__ dst, uint32_t* status) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
   const uint32_t s = inv[o];
+  if (!LJ_IDX_OK(s < (uint64_t)n, status)) return;
   dst[o] = src[s];
   dst[n + o] = src[n + s];
   dst[2 * n + o] = src[2 * n + s];
 }
 
-cudaError_t launch_from_slots(const uint32_t* inv, const double* src3, int64_t n, double* dst3, cudaStream_t s) {
-  k_from_slots<<<nb(n, 256), 256, 0, s>>>(inv, src3, n, dst3);
+cudaError_t launch_from_slots(const uint32_t* inv, const double* src3, int64_t n, double* dst3, cudaStream_t s,
+                              uint32_t* status) {
+  k_from_slots<<<nb(n, 256), 256, 0, s>>>(inv, src3, n, dst3, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s) {
-  k_to_original<<<nb(n, 256), 256, 0, s>>>(pos, src3, n, dst3);
+cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s,
+                               uint32_t* status) {
+  k_to_original<<<nb(n, 256), 256, 0, s>>>(pos, src3, n, dst3, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s) {
-  k_pos_to_original<<<nb(n, 256), 256, 0, s>>>(pos, n, dst3);
+cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s,
+                                   uint32_t* status) {
+  k_pos_to_original<<<nb(n, 256), 256, 0, s>>>(pos, n, dst3, status);
   return cudaGetLastError();
 }
 
@@ -228,13 +235,14 @@ cudaError_t launch_scale_check(Ctx& c) {
 // 0 < R^2 <= Rc2, j in the 27 cells around i.  With out == nullptr only counts.
 __global__ void k_lc_pairs(const uint4* __restrict__ pos, const uint32_t* __restrict__ cs, int nc, int64_t n,
                            uint64_t Rc2, unsigned long long* __restrict__ count, int2* __restrict__ out,
-                           unsigned long long cap) {
+                           unsigned long long cap, uint32_t* status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint4 pi = pos[i];
   const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
   Seg segs[18];
   const int ns = make_segments<false>(cs, nc, cz * nc + cy, cx, cx, 0u, 0u, segs);
+  check_segs(segs, ns, (uint32_t)n, status);
   for (int s = 0; s < ns; ++s)
     for (uint32_t j = segs[s].b; j < segs[s].e; ++j) {
       const uint4 pj = pos[j];
@@ -249,7 +257,7 @@ cudaError_t launch_lc_pairs(Ctx& c, unsigned long long* count, int2* out, size_t
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), c.stream);
   if (e != cudaSuccess) return e;
   k_lc_pairs<<<nb(c.n, 128), 128, 0, c.stream>>>(c.pos, c.cell_start, c.binned_nc, c.n, c.P.Rc2, count, out,
-                                                (unsigned long long)cap);
+                                                (unsigned long long)cap, c.status);
   return cudaGetLastError();
 }
 

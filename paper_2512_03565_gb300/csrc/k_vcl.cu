@@ -61,11 +61,13 @@ __global__ void k_tower_keys(const uint4* __restrict__ pos, int64_t n, const uin
 __global__ void k_permute_orig(const unsigned long long* __restrict__ key, int64_t n, const uint4* __restrict__ pos,
                                const double* __restrict__ vel, const double* __restrict__ frc,
                                uint4* __restrict__ pos2, double* __restrict__ vel2, double* __restrict__ frc2,
-                               uint32_t* __restrict__ inv, uint32_t* __restrict__ xb) {
+                               uint32_t* __restrict__ inv, uint32_t* __restrict__ xb, uint32_t* status) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= n) return;
   const uint32_t o = (uint32_t)(key[d] & 0xffffffffull);
+  if (!LJ_IDX_OK(o < (uint64_t)n, status)) return;
   const uint32_t s = inv[o];
+  if (!LJ_IDX_OK(s < (uint64_t)n, status)) return;
   const uint4 p = pos[s];
   pos2[d] = p;
   inv[o] = (uint32_t)d;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(256) k_vcl_build(VclBuildArgs A) {
         if (k < total) {
           const uint32_t r = k - o_ex;
           J = r < o_l1 ? o_s1 + r : o_s2 + (r - o_l1);
-          if (!HALF || J >= (uint32_t)I) {
+          if ((!HALF || J >= (uint32_t)I) && LJ_IDX_OK((int64_t)J < A.ncl, A.status)) {
             const uint4 lj = A.lo[J], hj = A.hi[J];
             const uint64_t dx = ivgap(li.x, hi.x, lj.x, hj.x);
             const uint64_t dy = ivgap(li.y, hi.y, lj.y, hj.y);
@@ -328,7 +330,7 @@ cudaError_t vcl_bin(Ctx& c, int M, int64_t* ncl_out) {
   unsigned long long* key2 = c.key + n;
   if ((e = sort_segments(c, c.cell_start, ncell, c.key, key2)) != cudaSuccess) return e;
   k_permute_orig<<<nblk(n, 256), 256, 0, c.stream>>>(key2, n, c.pos, c.vel, c.frc, c.pos_alt, c.vel_alt, c.frc_alt,
-                                                      c.inv, c.x_build);
+                                                      c.inv, c.x_build, c.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   std::swap(c.pos, c.pos_alt);
   std::swap(c.vel, c.vel_alt);

@@ -42,6 +42,10 @@ __global__ void __launch_bounds__(256) k_build_verlet(const uint4* __restrict__ 
     }
     BSeg segs[18];
     const int ns = builder_segments(cs, nc, (int)tile.z, cx, segs);
+#ifdef LJGB_CHECKS
+    for (int s = 0; s < ns; ++s)
+      if (!LJ_IDX_OK(segs[s].b <= segs[s].e && segs[s].e <= (uint32_t)n, status)) segs[s].b = segs[s].e = 0u;
+#endif
     const uint32_t my_cnt = bv_tile<HALF, COLMAJOR>(pos, segs, ns, tile.x, ni, s_i[wib], s_c[wib], n, cap, Rl2,
                                                      rl2p_lo, rl2p_hi, nbr);
     if (lane < ni) {
@@ -59,21 +63,23 @@ __global__ void __launch_bounds__(256) k_build_verlet(const uint4* __restrict__ 
 // rstart[j]..rstart[j+1] holds the entry ids e = k * n + i (column-major
 // slots) of all entries with nbr[e] = j, in ascending e.
 __global__ void k_rev_count(const int32_t* __restrict__ nbr, const int32_t* __restrict__ nnbr, int n, int cap,
-                            uint32_t* __restrict__ rcnt, uint32_t* __restrict__ rslot) {
+                            uint32_t* __restrict__ rcnt, uint32_t* __restrict__ rslot, uint32_t* status) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)cap * n) return;
   const int k = (int)(e / n), i = (int)(e % n);
   if (k >= min(nnbr[i], cap)) return;
+  if (!LJ_IDX_OK((unsigned)nbr[e] < (unsigned)n, status)) return;
   rslot[e] = atomicAdd(&rcnt[nbr[e]], 1u);
 }
 
 __global__ void k_rev_scatter(const int32_t* __restrict__ nbr, const int32_t* __restrict__ nnbr, int n, int cap,
                               const uint32_t* __restrict__ rstart, const uint32_t* __restrict__ rslot,
-                              unsigned long long* __restrict__ rkey) {
+                              unsigned long long* __restrict__ rkey, uint32_t* status) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)cap * n) return;
   const int k = (int)(e / n), i = (int)(e % n);
   if (k >= min(nnbr[i], cap)) return;
+  if (!LJ_IDX_OK((unsigned)nbr[e] < (unsigned)n, status)) return;
   rkey[rstart[nbr[e]] + rslot[e]] = (unsigned long long)e;
 }
 
@@ -82,13 +88,14 @@ template <typename R>
 __global__ void k_twopass_gather(int n, int cap, const uint32_t* __restrict__ rstart,
                                  const unsigned long long* __restrict__ rkey, const R* __restrict__ slot,
                                  double e24u, double* __restrict__ fx, double* __restrict__ fy,
-                                 double* __restrict__ fz) {
+                                 double* __restrict__ fz, uint32_t* status) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int64_t ne = (int64_t)cap * n;
   R sx = 0, sy = 0, sz = 0;
   for (uint32_t q = rstart[j]; q < rstart[j + 1]; ++q) {
     const int64_t e = (int64_t)rkey[q];
+    if (!LJ_IDX_OK(e < ne, status)) break;
     sx += slot[e];
     sy += slot[ne + e];
     sz += slot[2 * ne + e];
@@ -117,12 +124,14 @@ cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen
 // 16-bit copy of the lists: entry j stored as j - i wrapped into [-n/2, n/2);
 // any entry outside the int16 range sets *overflow (the 32-bit list is used).
 __global__ void k_list_to16(const int32_t* __restrict__ nbr, const int32_t* __restrict__ nnbr, int64_t n, int cap,
-                            int colmajor, int16_t* __restrict__ out, uint32_t* __restrict__ overflow) {
+                            int colmajor, int16_t* __restrict__ out, uint32_t* __restrict__ overflow,
+                            uint32_t* status) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)cap * n) return;
   const int64_t i = colmajor ? e % n : e / cap;
   const int k = colmajor ? (int)(e / n) : (int)(e % cap);
   if (k >= min(nnbr[i], cap)) return;
+  if (!LJ_IDX_OK((uint64_t)(uint32_t)nbr[e] < (uint64_t)n, status)) return;
   int64_t d = (int64_t)nbr[e] - i;
   if (d >= (n + 1) / 2) d -= n;
   if (d < -(n / 2)) d += n;
@@ -145,7 +154,8 @@ cudaError_t launch_list_to16(Ctx& c, uint32_t* overflow) {
   }
   cudaError_t e = cudaMemsetAsync(overflow, 0, sizeof(uint32_t), c.stream);
   if (e != cudaSuccess) return e;
-  k_list_to16<<<nb(ne, 256), 256, 0, c.stream>>>(c.nbr, c.nnbr, c.n, c.vl_cap, c.vl_colmajor, c.nbr16, overflow);
+  k_list_to16<<<nb(ne, 256), 256, 0, c.stream>>>(c.nbr, c.nnbr, c.n, c.vl_cap, c.vl_colmajor, c.nbr16, overflow,
+                                                  c.status);
   return cudaGetLastError();
 }
 
@@ -153,10 +163,11 @@ cudaError_t launch_reverse_index(Ctx& c) {
   const int64_t n = c.n, ne = (int64_t)c.vl_cap * n;
   cudaError_t e;
   if ((e = cudaMemsetAsync(c.rev_cnt, 0, (size_t)(n + 1) * sizeof(uint32_t), c.stream)) != cudaSuccess) return e;
-  k_rev_count<<<nb(ne, 256), 256, 0, c.stream>>>(c.nbr, c.nnbr, (int)n, c.vl_cap, c.rev_cnt, c.rev_slot);
+  k_rev_count<<<nb(ne, 256), 256, 0, c.stream>>>(c.nbr, c.nnbr, (int)n, c.vl_cap, c.rev_cnt, c.rev_slot,
+                                                 c.status);
   if ((e = excl_scan_u32(c, c.rev_cnt, c.rev_start, n)) != cudaSuccess) return e;
   k_rev_scatter<<<nb(ne, 256), 256, 0, c.stream>>>(c.nbr, c.nnbr, (int)n, c.vl_cap, c.rev_start, c.rev_slot,
-                                                   c.rev_key);
+                                                   c.rev_key, c.status);
   if ((e = sort_segments(c, c.rev_start, n, c.rev_key, c.rev_key2)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -166,11 +177,11 @@ cudaError_t launch_twopass_gather(Ctx& c) {
   if (c.prec == LJ_PREC_FP64)
     k_twopass_gather<double><<<nb(n, 256), 256, 0, c.stream>>>((int)n, c.vl_cap, c.rev_start, c.rev_key2,
                                                                (const double*)c.twopass, c.P.e24u, c.frc,
-                                                               c.frc + n, c.frc + 2 * n);
+                                                               c.frc + n, c.frc + 2 * n, c.status);
   else
     k_twopass_gather<float><<<nb(n, 256), 256, 0, c.stream>>>((int)n, c.vl_cap, c.rev_start, c.rev_key2,
                                                               (const float*)c.twopass, c.P.e24u, c.frc, c.frc + n,
-                                                              c.frc + 2 * n);
+                                                              c.frc + 2 * n, c.status);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,16 @@ enum : uint32_t {
   ST_TIMEOUT = 16u,   // a bounded wait gave up
 };
 
+// Index checks of the LJGB_CHECKS build (build.py): an index read from data
+// (a list entry, a segment bound, a cluster entry, a permutation slot) that
+// falls outside its array sets ST_OOB, and the kernel skips or substitutes the
+// access.  In the default build the test compiles away.
+#ifdef LJGB_CHECKS
+#define LJ_IDX_OK(cond, status) ((cond) ? true : (atomicOr((status), ST_OOB), false))
+#else
+#define LJ_IDX_OK(cond, status) true
+#endif
+
 // ---------------------------------------------------------------------------
 // Parameter block, passed by value to the force kernels.
 //
@@ -453,9 +463,11 @@ cudaError_t sort_segments(Ctx& c, const uint32_t* starts, int64_t nseg, unsigned
                           unsigned long long* key2);
 cudaError_t launch_build_verlet(Ctx& c, int half, int colmajor, uint32_t* maxlen);
 cudaError_t launch_update_pos(uint4* pos, const uint32_t* inv, const double* x, int64_t n, double L,
-                              const uint32_t* xb, uint64_t disp2_max, uint32_t* skin_flag, cudaStream_t s);
+                              const uint32_t* xb, uint64_t disp2_max, uint32_t* skin_flag, cudaStream_t s,
+                              uint32_t* status);
 cudaError_t launch_iota(uint32_t* inv, int64_t n, cudaStream_t s);
-cudaError_t launch_from_slots(const uint32_t* inv, const double* src3, int64_t n, double* dst3, cudaStream_t s);
+cudaError_t launch_from_slots(const uint32_t* inv, const double* src3, int64_t n, double* dst3, cudaStream_t s,
+                              uint32_t* status);
 cudaError_t launch_reverse_index(Ctx& c);
 cudaError_t launch_list_to16(Ctx& c, uint32_t* overflow);
 int vcl_ntower(int64_t n, int M);
@@ -482,8 +494,10 @@ cudaError_t force_vl_f64(Ctx& c, const lj_config& cfg, bool ev);
 cudaError_t launch_kick_drift(Ctx& c, double hdtm, double dtu, bool kick_only, bool track,
                               uint32_t* skin_flag = nullptr, double* zero_acc = nullptr, bool pre = false,
                               double hpre = 0.0);
-cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s);
-cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s);
+cudaError_t launch_to_original(const uint4* pos, const double* src3, int64_t n, double* dst3, cudaStream_t s,
+                               uint32_t* status);
+cudaError_t launch_pos_to_original(const uint4* pos, int64_t n, uint32_t* dst3, cudaStream_t s,
+                                   uint32_t* status);
 cudaError_t launch_feature_stats(Ctx& c, unsigned long long* stats);
 cudaError_t launch_ke(Ctx& c, double* out);
 cudaError_t launch_check_finite(Ctx& c);
