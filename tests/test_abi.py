@@ -125,3 +125,22 @@ def test_bench_tables_cover_every_configuration(lj):
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
     assert {c.newton3 for c in lj.configs()} <= set(bench.FLOPS_PER_PAIR)
+
+
+def test_index_check_build_compiles_and_exports_the_same_symbols(lj):
+    # LJGB_CHECKS=1 builds a second library whose kernels check every index
+    # they follow; it must compile and keep the ABI of the default build
+    import shutil
+    import subprocess
+    import sys
+    if shutil.which(os.environ.get("NVCC", "nvcc")) is None:
+        pytest.skip("nvcc not available")
+    env = dict(os.environ, LJGB_CHECKS="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "paper_2512_03565_gb300", "build.py")], env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    path = r.stdout.strip().splitlines()[-1]
+    assert os.path.basename(os.path.dirname(path)) == "_build_checks" and path != lj.LIB_PATH
+    lib = C.CDLL(path)
+    missing = [n for n in header_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
