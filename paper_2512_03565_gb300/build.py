@@ -33,11 +33,11 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src: str, hdr_mtime: float, verbose: bool) -> str:
-    obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, hdr_mtime: float, verbose: bool, out: str, flags: list[str]) -> str:
+    obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_mtime):
         return obj
-    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [NVCC, *ARCH, *flags, "-c", src, "-o", obj + ".tmp"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -47,22 +47,33 @@ def _compile(src: str, hdr_mtime: float, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, out: str | None = None,
+          host_flags: tuple[str, ...] = ()) -> str:
+    """Compiles into `out` (default: the in-tree build folder) and returns the
+    library's path.  `host_flags` go to the host compiler of every unit and of
+    the link (e.g. sanitizers for the host-side code); a build with them must
+    name its own `out`."""
+    if host_flags and out is None:
+        raise ValueError("a build with host_flags needs its own output folder")
+    out = out or OUT
+    lib = os.path.join(out, "libljgb.so")
+    os.makedirs(out, exist_ok=True)
+    xhost = [a for f in host_flags for a in ("-Xcompiler", f)]
+    flags = FLAGS + xhost
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hm = _headers_mtime()
     jobs = jobs or max(1, min(len(srcs), os.cpu_count() or 4))
     with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, hm, verbose), srcs))
-    if (not os.path.exists(LIB)) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [NVCC, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-ldl"]
+        objs = list(ex.map(lambda s: _compile(s, hm, verbose, out, flags), srcs))
+    if (not os.path.exists(lib)) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        cmd = [NVCC, *ARCH, *xhost, "-shared", "-o", lib + ".tmp", *objs, "-ldl"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":

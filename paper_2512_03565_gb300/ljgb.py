@@ -18,9 +18,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# LJGB_CHECKS=1 selects the build with device index checks (see build.py)
-LIB_PATH = os.path.join(_HERE, "_build_checks" if os.environ.get("LJGB_CHECKS", "0") not in ("", "0") else "_build",
-                        "libljgb.so")
+# LJGB_CHECKS=1 selects the build with device index checks (see build.py);
+# LJGB_LIB names another build of the same library (e.g. one with host-side
+# sanitizers)
+LIB_PATH = os.environ.get("LJGB_LIB") or os.path.join(
+    _HERE, "_build_checks" if os.environ.get("LJGB_CHECKS", "0") not in ("", "0") else "_build", "libljgb.so")
 
 # lj_status
 LJ_OK, LJ_ERR_ARG, LJ_ERR_CUDA, LJ_ERR_CAPACITY, LJ_ERR_SKIN, LJ_ERR_NONFINITE, LJ_ERR_TIMEOUT, \
