@@ -50,7 +50,9 @@ typedef struct lj_ctx lj_ctx;
 typedef enum {
   LJ_OK = 0,
   LJ_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad config) */
-  LJ_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  LJ_ERR_CUDA = 2,       /* a CUDA runtime call failed; in the index-check build (LJGB_CHECKS=1)
+                            also a kernel that met an index outside its array (lj_last_error:
+                            "device index check failed"); it skipped that access */
   LJ_ERR_CAPACITY = 3,   /* a Verlet list overflowed its capacity (the library regrows and rebuilds) */
   LJ_ERR_SKIN = 4,       /* a particle moved more than skin/2 since the last list build */
   LJ_ERR_NONFINITE = 5,  /* a force, energy or virial was NaN or infinite */
