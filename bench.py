@@ -308,7 +308,7 @@ def run_ours(args, ws, rank, local, pg):
         # the unit that binds this kernel (ncu): L1 data-pipe wavefronts of the
         # position gathers and list loads, ahead of issue slots and DRAM
         roof["limiter"] = {"unit": "L1 data pipe (LSU wavefronts)", "pct_of_peak": l1, "issue_active_pct": issue,
-                           "source": "ncu --set full, profiles/force_vl_jsplit4_c2.md"}
+                           "source": "ncu --metrics, profiles/force_c2_traffic.txt"}
 
     # end to end through the public API with host buffers, as a host-driven
     # time loop makes the calls: each step uploads that step's positions
