@@ -7,7 +7,8 @@
 //              nbr[k * n + i], so the k-th entries of 32 i's are one
 //              coalesced load.
 //   JSPLIT<w>  w lanes per i striding over its row-major list nbr[i * cap + k]
-//              with a w-lane shuffle reduction (1/V for w = 32, V2/2 for w = 2).
+//              with a w-lane shuffle reduction (1/V for w = 32, V2/2 for w = 2);
+//              for w = 2 each lane takes two adjacent entries per load.
 // With Newton-3 the lists are half lists (j after i in cell order) and every
 // pair's j contribution is scattered with FP64 atomics; the two-pass variant
 // writes each pair's contribution to its list slot and a second kernel sums a
@@ -142,6 +143,14 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
 template <typename R, int W, int N3, bool EV, bool I16>
 __global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
   constexpr int G = 32 / W;
+  // Two-lane groups read their list entries in pairs: lane sub takes
+  // entries 2 sub and 2 sub + 1 of every 4-entry chunk with one 8-byte load,
+  // so a warp's list load serves 4 entries of each of its 16 rows.  (Rows
+  // start on 32-byte boundaries: the capacity is a multiple of 8.)  Measured
+  // on the 1,048,576-particle fluid: w = 2 gains 6 %; w = 4 and 8 lose 1.5 %
+  // and 4 %, their gathers spreading over more lines than the loads save.
+  constexpr bool PAIRED = !I16 && W == 2;
+  static_assert(VL_BATCH % 2 == 0, "paired entries fill a batch");
   const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
   const int64_t n = P.n;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -154,8 +163,9 @@ __global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, Forc
     if (vi) {
       const uint4 pi = A.pos[i];
       const int m = min(A.nnbr[i], A.cap);
-      // running pointer to this lane's next entries of row i (entries k0 + t W)
-      const int32_t* rp = A.nbr + i * A.cap + sub;
+      // running pointer to this lane's next entries of row i (entries k0 + t W,
+      // or k0 + 2 W c + {0, 1} when paired)
+      const int32_t* rp = A.nbr + i * A.cap + (PAIRED ? 2 * sub : sub);
       const int16_t* rp16 = I16 ? A.nbr16 + i * A.cap + sub : nullptr;
       auto entry = [&](int off) -> int {
         if (I16) {
@@ -167,18 +177,33 @@ __global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, Forc
         const int j = __ldcs(rp + off);
         return LJ_IDX_OK((unsigned)j < (unsigned)n, A.status) ? j : (int)i;  // checks build: self, no pair
       };
-      int jc[VL_BATCH];
+      // the lane's VL_BATCH entries from rp on, k0 being the first one's index;
+      // entries past the row's end are i itself (R^2 = 0: no pair)
+      auto batch = [&](int k0, int (&jj)[VL_BATCH]) {
+        if constexpr (PAIRED) {
 #pragma unroll
-      for (int t = 0; t < VL_BATCH; ++t) jc[t] = (sub + t * W < m) ? entry(t * W) : (int)i;
-      for (int k0 = sub; k0 < m; k0 += W * VL_BATCH) {
+          for (int c = 0; c < VL_BATCH / 2; ++c) {
+            const int k = k0 + c * 2 * W;  // even, so k < m <= cap keeps k + 1 inside the row
+            int2 v = make_int2((int)i, (int)i);
+            if (k < m) v = __ldcs(reinterpret_cast<const int2*>(rp + c * 2 * W));
+            jj[2 * c] = LJ_IDX_OK((unsigned)v.x < (unsigned)n, A.status) ? v.x : (int)i;
+            jj[2 * c + 1] = (k + 1 < m && LJ_IDX_OK((unsigned)v.y < (unsigned)n, A.status)) ? v.y : (int)i;
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < VL_BATCH; ++t) jj[t] = (k0 + t * W < m) ? entry(t * W) : (int)i;
+        }
+      };
+      int jc[VL_BATCH];
+      batch(PAIRED ? 2 * sub : sub, jc);
+      for (int k0 = PAIRED ? 2 * sub : sub; k0 < m; k0 += W * VL_BATCH) {
         uint4 pj[VL_BATCH];
 #pragma unroll
         for (int t = 0; t < VL_BATCH; ++t) pj[t] = __ldg(A.pos + jc[t]);
         int jn[VL_BATCH];
         rp += W * VL_BATCH;
         if (I16) rp16 += W * VL_BATCH;
-#pragma unroll
-        for (int t = 0; t < VL_BATCH; ++t) jn[t] = (k0 + W * VL_BATCH + t * W < m) ? entry(t * W) : (int)i;
+        batch(k0 + W * VL_BATCH, jn);
 #pragma unroll
         for (int t = 0; t < VL_BATCH; ++t) {
           R af, bf, cf;
