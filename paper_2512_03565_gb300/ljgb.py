@@ -223,6 +223,13 @@ class Domain:
             self.lib.lj_destroy(self.h)
             self.h = _VP()
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def __del__(self):
         try:
             self.close()
@@ -446,6 +453,13 @@ class Ensemble:
         if self.h:
             self.lib.lj_ensemble_destroy(self.h)
             self.h = _VP()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:

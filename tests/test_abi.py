@@ -144,3 +144,25 @@ def test_index_check_build_compiles_and_exports_the_same_symbols(lj):
     lib = C.CDLL(path)
     missing = [n for n in header_symbols() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_handles_close_once_and_work_as_context_managers(lj, monkeypatch):
+    # the binding's lifetime rules, without a GPU: close() destroys the handle
+    # once, and leaving a with-block closes it
+    calls = []
+
+    class FakeLib:
+        def lj_destroy(self, h):
+            calls.append(("ctx", h.value))
+
+        def lj_ensemble_destroy(self, h):
+            calls.append(("ens", h.value))
+
+    for cls, kind in ((lj.Domain, "ctx"), (lj.Ensemble, "ens")):
+        obj = cls.__new__(cls)
+        obj.lib, obj.h = FakeLib(), lj._VP(1234)
+        with obj as o:
+            assert o is obj
+        assert calls[-1] == (kind, 1234) and not obj.h
+        obj.close()
+        assert len([c for c in calls if c[0] == kind]) == 1
