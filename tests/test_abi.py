@@ -166,3 +166,16 @@ def test_handles_close_once_and_work_as_context_managers(lj, monkeypatch):
         assert calls[-1] == (kind, 1234) and not obj.h
         obj.close()
         assert len([c for c in calls if c[0] == kind]) == 1
+
+
+def test_unit_rates_program_compiles(tmp_path):
+    # the per-SM throughput probe behind the FP32-pair design builds for sm_103a
+    import shutil
+    import subprocess
+    nvcc = os.environ.get("NVCC", "nvcc")
+    if shutil.which(nvcc) is None:
+        pytest.skip("nvcc not available")
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-c",
+                        os.path.join(ROOT, "paper_2512_03565_gb300", "unit_rates.cu"), "-o",
+                        str(tmp_path / "unit_rates.o")], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
