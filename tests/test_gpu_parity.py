@@ -461,3 +461,44 @@ def test_random_boxes_every_config(lj, seed):
         assert abs(U - U_ref) <= 1e-12 * max(abs(U_ref), 1e-300), (seed, lj.config_name(cfg))
         assert d.counters()[1] == np_ref, (seed, lj.config_name(cfg))
     d.close()
+
+
+def test_degenerate_sizes(lj):
+    """No particles is an argument error; one particle has no pair in any
+    configuration; two particles whose only pair crosses the periodic boundary
+    match the oracle in every configuration (FP64 and FP32 pair math); a lone
+    particle drifts ballistically under velocity Verlet."""
+    L, rc, skin = 4.0, 1.0, 0.3
+    u = L / 2 ** 32
+    d = lj.Domain(L, rc, skin, precision=lj.LJ_PREC_FP64)
+    with pytest.raises(lj.LJError, match="ARG"):
+        d.set_particles(np.zeros((3, 0), dtype=np.uint32))
+    one = np.array([[123456789], [2 ** 31], [7]], dtype=np.uint32)
+    d.set_particles(one)
+    for cfg in lj.configs():
+        U, W_ = d.compute_forces(cfg, energy=True)
+        assert np.array_equal(d.forces(), np.zeros((3, 1))), lj.config_name(cfg)
+        assert U == 0.0 and W_ == 0.0 and d.counters()[1] == 0, lj.config_name(cfg)
+    d.close()
+    half = int(round(0.45 / u))                    # separation 0.9 across the x = 0 face
+    two = np.array([[2 ** 32 - half, half], [2 ** 30, 2 ** 30], [5, 5]], dtype=np.uint32)
+    F_ref, U_ref, _, np_ref = oracle.forces_bruteforce(two, L, rc)
+    assert np_ref == 1 and F_ref[0, 1] > 0          # repulsive at 0.9: the pair pushes apart across the face
+    for prec in (lj.LJ_PREC_FP64, lj.LJ_PREC_FP32_ACC64):
+        d = lj.Domain(L, rc, skin, precision=prec)
+        d.set_particles(two)
+        for cfg in lj.configs():
+            U, _ = d.compute_forces(cfg, energy=True)
+            assert rel_err(d.forces(), F_ref) <= TOL[prec], (prec, lj.config_name(cfg))
+            assert abs(U - U_ref) <= ETOL[prec] * abs(U_ref), (prec, lj.config_name(cfg))
+            assert d.counters()[1] == 1, (prec, lj.config_name(cfg))
+        d.close()
+    d = lj.Domain(L, rc, skin, precision=lj.LJ_PREC_FP64)
+    x0 = np.array([[1.0], [2.0], [3.0]])
+    v0 = np.array([[0.5], [-0.25], [0.125]])
+    d.set_particles(x0, v0)
+    d.integrate(0.002, 10, lj.config(lj.LJ_LC, lj.LJ_ORD_IPT_SMEM))
+    x = d.state()[0].astype(np.float64) * u
+    # quantisation (< 1 unit) plus one rounding to the nearest unit per drift
+    np.testing.assert_allclose(x, np.mod(x0 + 10 * 0.002 * v0, L), rtol=0, atol=12 * u)
+    d.close()
