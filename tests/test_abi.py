@@ -125,6 +125,13 @@ def test_bench_tables_cover_every_configuration(lj):
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
     assert {c.newton3 for c in lj.configs()} <= set(bench.FLOPS_PER_PAIR)
+    # the committed ncu figures of the benched kernel parse, and the traffic is
+    # at least the list entries and positions one launch must read
+    traffic = bench.from_profiles("traffic", "VL:JSPLIT-4:N3off")
+    assert traffic is not None and traffic > 303e6
+    assert 0 < bench.from_profiles("l1_lsu_pct", "VL:JSPLIT-4:N3off") <= 100
+    assert 0 < bench.from_profiles("issue_pct", "VL:JSPLIT-4:N3off") <= 100
+    assert bench.from_profiles("traffic", "no such configuration") is None
 
 
 def test_index_check_build_compiles_and_exports_the_same_symbols(lj):
