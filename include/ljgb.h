@@ -235,8 +235,11 @@ lj_status lj_tune(lj_ctx* ctx, int32_t kind, int32_t samples, lj_config* chosen,
  * lj_energy_read: *mj = the counter of CUDA device `device` (-1 = current) in
  * millijoules since the driver loaded.
  *
- * lj_energy_period: polls the counter for probe_ms and returns in *period_ms
- * the median interval between its updates (NaN if fewer than 3 updates).
+ * lj_energy_period: polls the counter until it has updated 5 times or probe_ms
+ * has passed, and returns in *period_ms the median interval between
+ * consecutive updates (the one interval seen when only 2 updates came; NaN when
+ * fewer than 2 did).  A probe_ms of at least 10 counter periods (about 1 s on
+ * GB300) makes the NaN case mean a counter that is not updating.
  *
  * lj_tune_energy: full search by energy.  Every valid configuration runs a
  * warm-up evaluation, then a batch of force evaluations lasting at least

@@ -98,12 +98,17 @@ lj_status lj_energy_period(int32_t device, double probe_ms, double* period_ms) {
   nvmlDevice_t h;
   lj_status st = device_handle(device, &h);
   if (st != LJ_OK) return st;
+  // Polls until kWanted updates have been seen or probe_ms has passed.  The
+  // first update only marks a phase (the poll starts at an arbitrary point of
+  // the counter's period), so k updates give k - 1 whole intervals.
+  constexpr size_t kWanted = 5;
   using clk = std::chrono::steady_clock;
   const auto t0 = clk::now();
   double last = 0.0, v = 0.0;
   if ((st = read_mj(h, &last)) != LJ_OK) return st;
   std::vector<double> ticks;
-  while (std::chrono::duration<double, std::milli>(clk::now() - t0).count() < probe_ms) {
+  while (ticks.size() < kWanted &&
+         std::chrono::duration<double, std::milli>(clk::now() - t0).count() < probe_ms) {
     if ((st = read_mj(h, &v)) != LJ_OK) return st;
     if (v != last) {
       ticks.push_back(std::chrono::duration<double, std::milli>(clk::now() - t0).count());
@@ -111,7 +116,7 @@ lj_status lj_energy_period(int32_t device, double probe_ms, double* period_ms) {
     }
     std::this_thread::sleep_for(std::chrono::microseconds(200));
   }
-  if (ticks.size() < 3) {
+  if (ticks.size() < 2) {
     *period_ms = std::numeric_limits<double>::quiet_NaN();
     return LJ_OK;
   }

@@ -511,6 +511,9 @@ extern "C" lj_status lj_bin_cells_static(const uint32_t* pos_fp, int64_t n, int3
   const int64_t ncell = (int64_t)nc * nc * nc;
   if (ncell > kStaticMaxCells) return LJ_ERR_ARG;
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  // an error left by earlier, unrelated work on this thread is not this
+  // call's: clear it, so that the launch checks below see only these launches
+  (void)cudaGetLastError();
   void* base = nullptr;
   if (static_scratch(&base) != cudaSuccess) return LJ_ERR_CUDA;
   unsigned char* b = (unsigned char*)base;
@@ -523,12 +526,18 @@ extern "C" lj_status lj_bin_cells_static(const uint32_t* pos_fp, int64_t n, int3
   // the counters keep the previous call's values: clear them first
   if (cudaMemsetAsync(cnt, 0, (size_t)ncell * sizeof(uint32_t), s) != cudaSuccess) return LJ_ERR_CUDA;
   k_cell_ids_soa<<<nblk(n, 256), 256, 0, s>>>(pos_fp, n, (uint32_t)nc, cell_of, slot, cnt);
+  if (cudaGetLastError() != cudaSuccess) return LJ_ERR_CUDA;
   const int64_t nb = (ncell + SCAN_TILE - 1) / SCAN_TILE;
   k_scan_tiles<<<(unsigned)nb, SCAN_T, 0, s>>>(cnt, cell_start, ncell, scan_tot);
+  if (cudaGetLastError() != cudaSuccess) return LJ_ERR_CUDA;
   k_scan_totals<<<1, SCAN_T, 0, s>>>(scan_tot, nb, cell_start + ncell);
+  if (cudaGetLastError() != cudaSuccess) return LJ_ERR_CUDA;
   k_scan_add<<<(unsigned)nb, SCAN_T, 0, s>>>(cell_start, ncell, scan_tot);
+  if (cudaGetLastError() != cudaSuccess) return LJ_ERR_CUDA;
   k_scatter_keys_soa<<<nblk(n, 256), 256, 0, s>>>(n, cell_of, slot, cell_start, key);
+  if (cudaGetLastError() != cudaSuccess) return LJ_ERR_CUDA;
   k_sort_cells<<<nblk(ncell * 32, 256), 256, 0, s>>>(cell_start, ncell, key, key2);
+  if (cudaGetLastError() != cudaSuccess) return LJ_ERR_CUDA;
   k_keys_to_perm<<<nblk(n, 256), 256, 0, s>>>(key2, n, perm);
   return cudaGetLastError() == cudaSuccess ? LJ_OK : LJ_ERR_CUDA;
 }

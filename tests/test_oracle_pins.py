@@ -556,3 +556,65 @@ def test_half_shells_cover_every_pair_once(orc, backward):
         assert len(got) == len(set(got)), name                      # no pair twice
         bf = {tuple(int(v) for v in p) for p in orc.pairs_bruteforce(pos, L, 1.0)}
         assert set(got) == bf, name
+
+
+# --- sampled forces (the checker of the full-size GPU runs) --------------------
+
+def _sampled_cases():
+    rng = np.random.default_rng(7)
+    out = []
+    s = W.uniform(300, 0.8, 71)
+    out.append(("uniform", s.L, s.pos))
+    s = W.stratified(400, 0.5, 72)
+    out.append(("stratified", s.L, s.pos))
+    # pairs that interact only through a periodic face on each axis
+    L = 8.0
+    u = L / TWO32
+    face = np.zeros((3, 6), dtype=np.uint32)
+    for a in range(3):
+        face[:, 2 * a] = int(round(4.0 / u))
+        face[:, 2 * a + 1] = int(round(4.0 / u))
+        face[a, 2 * a] = int(round(0.4 / u))
+        face[a, 2 * a + 1] = TWO32 - int(round(0.9 / u))
+    out.append(("faces", L, face))
+    # a crowded cluster: 60 particles within 1.2 sigma of one point, in a dilute box
+    s = W.stratified(200, 0.1, 73)
+    crowd = (np.array([[2 ** 31], [2 ** 30], [2 ** 29]], dtype=np.int64)
+             + rng.integers(-int(0.6 / (s.L / TWO32)), int(0.6 / (s.L / TWO32)), size=(3, 60)))
+    pos = np.concatenate([s.pos.astype(np.int64), crowd], axis=1) % TWO32
+    out.append(("crowded", s.L, pos.astype(np.uint32)))
+    return out
+
+
+@pytest.mark.parametrize("name,L,pos", _sampled_cases(), ids=lambda v: v if isinstance(v, str) else "")
+def test_sampled_forces_equal_bruteforce_rows(orc, name, L, pos):
+    """forces_sampled(idx) must be the idx columns of the brute-force forces,
+    bit for bit (each row is the same ascending-j loop of Eq. 1), for any index
+    subset: repeated, unordered, first and last particle included."""
+    n = pos.shape[1]
+    F, _, _, npairs = orc.forces_bruteforce(pos, L, 2.5)
+    assert npairs > 0
+    rng = np.random.default_rng(n)
+    idx = np.concatenate([[0, n - 1, n - 1], rng.permutation(n)[: max(1, n // 3)], [n // 2, 0]])
+    Fs = orc.forces_sampled(pos, L, 2.5, idx)
+    assert Fs.shape == (3, idx.shape[0])
+    assert np.array_equal(Fs, F[:, idx])
+    assert np.array_equal(orc.forces_sampled(pos, L, 2.5, np.arange(n)), F)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sampled_forces_two_particle_textbook_value(orc, axis):
+    """Against the printed F(r) directly (not through the brute force): both
+    particles of an isolated pair at r = 2 get -/+ F(2) along the axis."""
+    L = 8.0
+    d = int(round(2.0 / (L / TWO32)))
+    pos = two_particles(L, d, axis, base=2 ** 31)
+    Fs = orc.forces_sampled(pos, L, 2.5, np.array([1, 0]))   # columns: particle 1, then particle 0
+    # the radial force F(r) (positive = repulsive) acts on particle 0, the
+    # lower one, along -axis
+    assert Fs[axis, 1] == pytest.approx(-GOLD["F_at_2"], rel=1e-11)
+    assert Fs[axis, 0] == -Fs[axis, 1]
+    assert np.all(Fs[[a for a in range(3) if a != axis]] == 0.0)
+    # beyond the cutoff on the sampled side too
+    far = two_particles(L, int(round(2.6 / (L / TWO32))), axis)
+    assert np.all(orc.forces_sampled(far, L, 2.5, np.array([0, 1])) == 0.0)
