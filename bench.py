@@ -39,9 +39,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell SM: 4 partitions x 32)
 FLOPS_PER_PAIR = {0: 23, 1: 26, 2: 26, 3: 26}   # useful flops per unique pair by Newton-3 mode
 WORKLOAD = ("homogeneous LJ fluid, 1,048,576 particles, density 0.75 (L=111.82), rc 2.5, skin 0.3 "
             "(Verlet rebuild every 10 steps), T=1.0 Maxwell-Boltzmann, velocity Verlet dt=0.002, "
@@ -147,15 +145,35 @@ def from_profiles(key, cfg_name):
     """A figure of the committed ncu summary of the force kernel, if it was
     taken for this configuration (lines: '<key> <config> <value>'; keys:
     traffic = DRAM bytes per launch, l1_lsu_pct / issue_pct = L1 data-pipe
-    wavefronts and issue slots, % of peak)."""
+    wavefronts and issue slots, % of peak; commit = the commit the capture
+    was taken at)."""
     path = os.path.join(ROOT, "profiles", "force_c2_traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         parts = line.split()
         if len(parts) == 3 and parts[0] == key and parts[1] == cfg_name:
-            return float(parts[2])
+            return parts[2] if key == "commit" else float(parts[2])
     return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def algorithmic_bytes(cfg, n, list_entries):
+    """Bytes a force evaluation must move at least, per launch: every
+    position read once (16 B: x, y, z fixed point and the original index),
+    the forces written (3 FP64; read and written with Newton-3, whose
+    contributions are added), and for Verlet lists the list entries (4 B
+    each) and lengths (4 B per particle)."""
+    pos = 16.0 * n
+    frc = (48.0 if cfg.newton3 != 0 else 24.0) * n
+    lists = 4.0 * float(list_entries) + 4.0 * n if cfg.container == 1 and list_entries is not None else 0.0
+    return pos + frc + lists
 
 
 def cpu_oracle_rate(system, evals_max=500, budget_s=25.0, min_s=10.0):
@@ -282,31 +300,50 @@ def run_ours(args, ws, rank, local, pg):
     value = pairs_all / total_s_all
 
     # roofline of the dominant kernel (the force kernel): useful FP32 flops of
-    # the unique in-cutoff pairs per launch / mean launch duration
+    # the unique in-cutoff pairs per launch / mean launch duration, against
+    # the FP32 peak of this device (SM count from the device, SM clock the
+    # maximum nvidia-smi reported during the timed region)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = int(props.multi_processor_count)
+    sm_max = float(clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
     avg_force_s = (force_ms / max(force_n, 1)) / 1e3
     flops_launch = FLOPS_PER_PAIR[cfg.newton3] * float(np.mean(pairs))
     achieved = flops_launch / avg_force_s / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     traffic = from_profiles("traffic", cfg_name)
+    list_entries = None
+    if cfg.container == lj.LJ_VL:
+        nn = np.zeros(s.n, dtype=np.int32)
+        capv = lj.C.c_int32()
+        if lj.load().lj_get_verlet(d.h, None, nn.ctypes.data, lj.C.byref(capv)) == lj.LJ_OK:
+            list_entries = int(nn.astype(np.int64).sum())
+    alg_bytes = algorithmic_bytes(cfg, s.n, list_entries)
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel_ms": avg_force_s * 1e3,
-            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FFMA)",
-            "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3],
+            "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
+                          "(SM count from the device, clock from nvidia-smi during the run; derived FFMA peak)",
+            "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3], "pairs_per_launch": float(np.mean(pairs)),
             # the kernel's own pair evaluations (Newton-3 off evaluates each pair from both sides)
-            "kernel_pair_evals_per_s": (2.0 if cfg.newton3 == 0 else 1.0) * float(np.mean(pairs)) / avg_force_s}
+            "kernel_pair_evals_per_s": (2.0 if cfg.newton3 == 0 else 1.0) * float(np.mean(pairs)) / avg_force_s,
+            # the same launch against the memory roofline: algorithmic bytes
+            # (list entries + lengths, positions, forces) per launch / launch time
+            "alg_bytes": alg_bytes, "list_entries": list_entries, "hbm_peak_gbs": hbm_peak,
+            "hbm_alg_gbs": alg_bytes / avg_force_s / 1e9,
+            "hbm_alg_frac": alg_bytes / avg_force_s / 1e9 / hbm_peak}
     if traffic:
-        hbm_peak = 6800.0
-        try:
-            hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
-        except Exception:
-            pass
+        # DRAM bytes of one launch from the committed ncu capture (a cross-check
+        # taken at the commit named in the same file)
+        roof["traffic_source"] = {"file": "profiles/force_c2_traffic.txt",
+                                  "commit": from_profiles("commit", cfg_name)}
         roof["hbm_gbs"] = traffic / avg_force_s / 1e9
         roof["hbm_frac"] = roof["hbm_gbs"] / hbm_peak
-        roof["hbm_peak_gbs"] = hbm_peak
+        roof["traffic_over_alg"] = traffic / alg_bytes
     l1, issue = from_profiles("l1_lsu_pct", cfg_name), from_profiles("issue_pct", cfg_name)
     if l1 is not None:
-        # the unit that binds this kernel (ncu): L1 data-pipe wavefronts of the
-        # position gathers and list loads, ahead of issue slots and DRAM
+        # the units that bind this kernel (ncu): L1 data-pipe wavefronts of the
+        # position gathers and list loads, then issue slots; DRAM is not the limit
         roof["limiter"] = {"unit": "L1 data pipe (LSU wavefronts)", "pct_of_peak": l1, "issue_active_pct": issue,
                            "source": "ncu --metrics, profiles/force_c2_traffic.txt"}
 

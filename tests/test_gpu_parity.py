@@ -67,6 +67,26 @@ def test_every_config_matches_oracle(lj, sys_small, ref_small, prec):
     assert not bad, bad
 
 
+def test_fp32_error_on_the_densest_workload(lj):
+    """FP32 pair math sums a lane's contributions in FP32 before the FP64
+    fold: a whole Verlet list in VL_IPT (about 120 entries at density 1.2),
+    every linked-cell candidate in the IPT and KI orders.  On the densest
+    workload (jittered FCC at density 1.2, the top of the density sweep) every
+    configuration stays within the FP32 bound 1e-5 of max |dF| / RMS |F|."""
+    s = W.fcc(6000, 1.2, 171)
+    F_ref, U_ref, _, np_ref = ref_forces(s)
+    d = lj.Domain(s.L, s.rc, s.skin, precision=1)
+    d.set_particles(s.pos, s.vel)
+    errs = {}
+    for cfg in lj.configs():
+        d.compute_forces(cfg)
+        errs[lj.config_name(cfg)] = rel_err(d.forces(), F_ref)
+        assert d.counters()[1] == np_ref
+    d.close()
+    worst = max(errs, key=errs.get)
+    assert errs[worst] <= TOL[1], (worst, errs[worst])
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_config1_uniform_1000(lj, prec):
     """1,000 particles, uniform random at density 0.8, rc 2.5, one evaluation."""
