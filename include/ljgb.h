@@ -168,12 +168,14 @@ lj_status lj_build_verlet(lj_ctx* ctx, int32_t half_list);
  * k^3 M <= n; tower of a particle (floor(x_fp n_t / 2^32), floor(y_fp n_t /
  * 2^32)); storage by tower id cx n_t + cy, then z_fp, then original index.
  * Each tower's run is cut into clusters of M consecutive particles (the last
- * one shorter).  A cluster's box is the min/max of its fixed-point
- * coordinates; clusters I and J are neighbours iff the sum over the axes of
- * the squared periodic distances between their boxes' intervals is at most
- * floor(((r_c + skin)/u)^2), decided in 64-bit integers.  Full lists hold
- * every neighbour J (I itself included); half lists (half_list = 1, for
- * Newton-3) only J >= I.  Grows the list capacity and rebuilds on overflow.
+ * one shorter).  Clusters I and J are neighbours iff some member pair (two
+ * different particles, one of each) lies within r_c + skin by the exact
+ * integer rule; the search prunes by the clusters' boxes (min/max of their
+ * fixed-point coordinates) and records each listed pair's member mask
+ * (lj_get_cluster_masks).  Full lists hold every neighbour J (I itself when
+ * two of its members are within range); half lists (half_list = 1, for
+ * Newton-3) only J >= I, with the pairs of I itself counted once.  Grows the
+ * list capacity and rebuilds on overflow.
  * Errors: LJ_ERR_ARG (M not 4, 6 or 8; n >= 2^29), LJ_ERR_STATE,
  * LJ_ERR_CAPACITY, LJ_ERR_OOM, LJ_ERR_CUDA. */
 lj_status lj_build_clusters(lj_ctx* ctx, int32_t M, int32_t half_list);
@@ -190,6 +192,17 @@ lj_status lj_get_clusters(lj_ctx* ctx, int64_t* ncl, uint32_t* cl_start, int32_t
  * is defined; the order is not); *cap_out the capacity.  Either array may be
  * NULL.  Errors: LJ_ERR_STATE if no cluster list is current. */
 lj_status lj_get_cluster_lists(lj_ctx* ctx, int32_t* nbr, int32_t* nn, int32_t* cap_out);
+
+/* The member masks of the cluster-pair lists (Sec. 2.1.1, Verlet cluster
+ * lists; the paper gives no bit layout, this one is the library's): masks
+ * (host, [ncl][cap] uint64, row-major, in the order of lj_get_cluster_lists'
+ * entries, 0 beyond a list's length).  Bit a * M + b of an entry (I, J) is set
+ * iff the a-th particle of cluster I and the b-th of J (in cluster order, M
+ * the cluster size) are two different particles within r_c + skin, for a
+ * half list's entry J = I only with b > a.  A cluster pair is listed iff its
+ * mask is not empty; the force kernels take exactly the pairs of set bits.
+ * Errors: LJ_ERR_ARG (null), LJ_ERR_STATE if no cluster list is current. */
+lj_status lj_get_cluster_masks(lj_ctx* ctx, uint64_t* masks);
 
 /* One force evaluation F_i = sum_j F_ij (Eq. 1) with the given configuration.
  * LC rebins; VL and VCL build their lists when they are stale (never built,

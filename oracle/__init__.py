@@ -36,6 +36,7 @@ _U32P = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 _I32P = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _I64P = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 _F64P = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_U64P = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
@@ -85,7 +86,8 @@ def _load():
             "orc_features": (i32, [i64, _U32P, _U32P, _U32P, f64, f64, f64, _F64P]),
             "orc_vcl_ntower": (i32, [i64, i32]),
             "orc_vcl_order": (i64, [i64, _U32P, _U32P, _U32P, i32, _U32P, _U32P]),
-            "orc_vcl_lists": (i32, [i64, _U32P, _U32P, _U32P, _U32P, _U32P, f64, f64, i32, i32, _I32P, _I32P]),
+            "orc_vcl_lists": (i32, [i64, _U32P, _U32P, _U32P, _U32P, _U32P, f64, f64, i32, i32, i32, _I32P, _I32P,
+                                    _U64P]),
             "orc_mlp_nparams": (i64, [i32]),
             "orc_mlp_forward": (None, [_F64P, i32, i64, _F64P, _F64P]),
             "orc_mlp_loss_grad": (f64, [_F64P, i32, i64, _F64P, _F64P, _F64P, _F64P]),
@@ -226,19 +228,26 @@ def vcl_order(pos, M):
     return perm, cls[:ncl + 1].copy()
 
 
-def vcl_lists(pos, L, rl, M, half):
-    """Cluster-pair lists by brute force over all cluster pairs (reading R19).
-    Returns (perm, cl_start, lists): lists[I] the ascending neighbour clusters of I."""
+def vcl_lists(pos, L, rl, M, half, masks=False):
+    """Cluster-pair lists by brute force over all cluster pairs and their
+    member pairs (readings R19, R21): I lists J iff some member pair lies
+    within r_l.  Returns (perm, cl_start, lists): lists[I] the ascending
+    neighbour clusters of I; with masks=True also the per-entry member masks
+    (bit a * M + b for the a-th member of I and the b-th of J)."""
     x, y, z = _soa(pos)
     perm, cls = vcl_order(pos, M)
     ncl = cls.shape[0] - 1
     nn = np.zeros(max(ncl, 1), dtype=np.int32)
     cap = max(ncl, 1)
     nbr = np.zeros((max(ncl, 1), cap), dtype=np.int32)
-    r = _load().orc_vcl_lists(ncl, perm, cls, x, y, z, L, rl, int(bool(half)), cap, nbr, nn)
+    mk = np.zeros((max(ncl, 1), cap), dtype=np.uint64)
+    r = _load().orc_vcl_lists(ncl, perm, cls, x, y, z, L, rl, int(bool(half)), int(M), cap, nbr, nn, mk)
     if r != 0:
         raise ValueError("cluster lists failed")
-    return perm, cls, [nbr[I, :nn[I]].copy() for I in range(ncl)]
+    lists = [nbr[I, :nn[I]].copy() for I in range(ncl)]
+    if masks:
+        return perm, cls, lists, [mk[I, :nn[I]].copy() for I in range(ncl)]
+    return perm, cls, lists
 
 
 def forces_cells(pos, L, rc, eps=1.0, sigma=1.0):

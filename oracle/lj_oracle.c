@@ -429,61 +429,50 @@ int64_t orc_vcl_order(int64_t n, const uint32_t* x, const uint32_t* y, const uin
   return ncl;
 }
 
-/* periodic distance of the intervals [a0, a1] and [b0, b1] (no wrap inside
- * either) on the circle of 2^32 fixed-point units */
-static inline uint64_t interval_gap(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
-  if (a0 <= b1 && b0 <= a1) return 0;
-  const uint32_t g1 = b0 - a1, g2 = a0 - b1; /* forward and backward gaps, mod 2^32 */
-  return g1 < g2 ? g1 : g2;
-}
 
-/* Cluster-pair lists by brute force over all cluster pairs (reading R19).
- * perm / cl_start as from orc_vcl_order; x, y, z in original order.  nbr is
- * row-major [ncl][cap] of cluster indices in ascending order, nn[ncl] the
- * complete list lengths (entries beyond cap are dropped).  Returns 0, 1 if a
- * list exceeded cap, -1 on bad arguments. */
+/* Cluster-pair lists by brute force over all cluster pairs and all their
+ * member pairs (readings R19 and R21).  perm / cl_start as from
+ * orc_vcl_order; x, y, z in original order.  I lists J iff some member pair
+ * (the a-th particle of I, the b-th of J, two different particles) lies
+ * within r_l: 0 < R^2 <= floor((r_l/u)^2).  Half lists (half = 1) keep J >= I
+ * and, for J = I, the pairs with b > a.  masks (may be NULL) receives per
+ * listed pair the bits a * M + b of those member pairs (M the cluster size,
+ * at most 8, so 64 bits suffice; every cluster holds at most M).  nbr is row-major
+ * [ncl][cap] of cluster indices in ascending order, nn[ncl] the complete list
+ * lengths (entries beyond cap are dropped).  Returns 0, 1 if a list exceeded
+ * cap, -1 on bad arguments. */
 int orc_vcl_lists(int64_t ncl, const uint32_t* perm, const uint32_t* cl_start, const uint32_t* x,
-                  const uint32_t* y, const uint32_t* z, double L, double rl, int half, int cap, int32_t* nbr,
-                  int32_t* nn) {
-  if (ncl < 0) return -1;
+                  const uint32_t* y, const uint32_t* z, double L, double rl, int half, int M, int cap,
+                  int32_t* nbr, int32_t* nn, uint64_t* masks) {
+  if (ncl < 0 || M < 1 || M > 8) return -1;
+  for (int64_t c = 0; c < ncl; ++c)
+    if (cl_start[c + 1] - cl_start[c] > (uint32_t)M) return -1;
   const uint64_t R2max = orc_cut2_int(L, rl);
-  uint32_t* bb = (uint32_t*)malloc(sizeof(uint32_t) * 6 * (size_t)(ncl > 0 ? ncl : 1));
-  if (!bb) return -1;
-  for (int64_t c = 0; c < ncl; ++c) {
-    uint32_t* b = bb + 6 * c;
-    const uint32_t p0 = perm[cl_start[c]];
-    b[0] = b[1] = x[p0];
-    b[2] = b[3] = y[p0];
-    b[4] = b[5] = z[p0];
-    for (uint32_t k = cl_start[c] + 1; k < cl_start[c + 1]; ++k) {
-      const uint32_t p = perm[k];
-      if (x[p] < b[0]) b[0] = x[p];
-      if (x[p] > b[1]) b[1] = x[p];
-      if (y[p] < b[2]) b[2] = y[p];
-      if (y[p] > b[3]) b[3] = y[p];
-      if (z[p] < b[4]) b[4] = z[p];
-      if (z[p] > b[5]) b[5] = z[p];
-    }
-  }
   int over = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(| : over)
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : over)
   for (int64_t I = 0; I < ncl; ++I) {
-    const uint32_t* a = bb + 6 * I;
     int cnt = 0;
     for (int64_t J = half ? I : 0; J < ncl; ++J) {
-      const uint32_t* b = bb + 6 * J;
-      const uint64_t dx = interval_gap(a[0], a[1], b[0], b[1]);
-      const uint64_t dy = interval_gap(a[2], a[3], b[2], b[3]);
-      const uint64_t dz = interval_gap(a[4], a[5], b[4], b[5]);
-      const uint64_t D2 = dx * dx + dy * dy + dz * dz;
-      if (D2 > R2max) continue;
-      if (cnt < cap) nbr[I * cap + cnt] = (int32_t)J;
+      uint64_t mask = 0;
+      for (uint32_t a = 0; a < cl_start[I + 1] - cl_start[I]; ++a) {
+        const uint32_t p = perm[cl_start[I] + a];
+        for (uint32_t b = 0; b < cl_start[J + 1] - cl_start[J]; ++b) {
+          if (J == I && (half ? b <= a : b == a)) continue;
+          const uint32_t q = perm[cl_start[J] + b];
+          const uint64_t R2 = r2int(mimg(x[p], x[q]), mimg(y[p], y[q]), mimg(z[p], z[q]));
+          if (R2 != 0 && R2 <= R2max) mask |= 1ull << (a * (uint32_t)M + b);
+        }
+      }
+      if (!mask) continue;
+      if (cnt < cap) {
+        nbr[I * cap + cnt] = (int32_t)J;
+        if (masks) masks[I * cap + cnt] = mask;
+      }
       ++cnt;
     }
     nn[I] = cnt;
     if (cnt > cap) over = 1;
   }
-  free(bb);
   return over;
 }
 

@@ -315,11 +315,14 @@ lj_status do_build_vcl(Ctx& c, int M, int half) {
     c.vcl_cap = (int)std::min<double>(std::ceil(m / 8.0) * 8.0, (double)std::max<int64_t>(ncl, 8) + 8.0);
   }
   for (int attempt = 0; attempt < 4; ++attempt) {
-    if (c.vcl_nbr_cap < (size_t)c.vcl_cap * ncl || !c.vcl_nbr) {
+    if (c.vcl_nbr_cap < (size_t)c.vcl_cap * ncl || !c.vcl_nbr || !c.vcl_mask) {
       dfree(c.vcl_nbr);
+      dfree(c.vcl_mask);
       c.vcl_nbr = nullptr;
+      c.vcl_mask = nullptr;
       c.vcl_nbr_cap = 0;
       CK(cudaMalloc(&c.vcl_nbr, (size_t)c.vcl_cap * ncl * sizeof(uint32_t)));
+      CK(cudaMalloc(&c.vcl_mask, (size_t)c.vcl_cap * ncl * sizeof(uint64_t)));
       c.vcl_nbr_cap = (size_t)c.vcl_cap * ncl;
     }
     if (c.vcl_nn_cap < (size_t)ncl || !c.vcl_nn) {
@@ -783,6 +786,20 @@ lj_status lj_get_cluster_lists(lj_ctx* h, int32_t* nbr, int32_t* nn, int32_t* ca
   return LJ_OK;
 }
 
+lj_status lj_get_cluster_masks(lj_ctx* h, uint64_t* masks) {
+  if (!h || !masks) return LJ_ERR_ARG;
+  Ctx& c = h->c;
+  if (!c.vcl_valid || c.binned_for != LJ_VCL) return fail(c, LJ_ERR_STATE, "no cluster list built");
+  const size_t ncl = (size_t)c.vcl_ncl, cap = (size_t)c.vcl_cap;
+  std::vector<int32_t> len(ncl);
+  CK(cudaMemcpyAsync(masks, c.vcl_mask, ncl * cap * sizeof(uint64_t), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(len.data(), c.vcl_nn, ncl * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  for (size_t I = 0; I < ncl; ++I)
+    for (size_t k = (size_t)std::max(0, std::min(len[I], (int32_t)cap)); k < cap; ++k) masks[I * cap + k] = 0;
+  return LJ_OK;
+}
+
 int32_t lj_config_valid(lj_config cfg) { return order_is_valid(cfg) ? 1 : 0; }
 
 int32_t lj_config_list(lj_config* out, int32_t cap) {
@@ -1131,7 +1148,7 @@ void lj_destroy(lj_ctx* h) {
                  c.key, c.scan_tmp, c.tiles, c.row_tiles, c.nbr, c.nnbr, c.x_build, c.maxlen, c.twopass,
                  c.rev_cnt, c.rev_start, c.rev_slot, c.rev_key, c.rev_key2, c.ev, c.status,
                  c.feat_stats, c.tile_ctr, c.stage, c.nbr16, c.tower_cl, c.cl_start, c.cl_lo, c.cl_hi, c.cl_z,
-                 c.vcl_nbr, c.vcl_nn};
+                 c.vcl_nbr, c.vcl_mask, c.vcl_nn};
   for (void* p : dev) dfree(p);
   if (c.host_ev) cudaFreeHost(c.host_ev);
   if (c.host_np) cudaFreeHost(c.host_np);

@@ -22,10 +22,11 @@
 //
 // The pair arithmetic is the same exact-cutoff kernel as the other
 // containers, evaluated branch-free (most candidates of a cluster pair are
-// outside the cutoff, and the warp would take the branch anyway).  Slots of
-// a neighbour cluster beyond its size, and the pairs of the base cluster with
-// itself that the Newton-3 half does not own, enter as a zero difference,
-// which the rule 0 < R^2 excludes.
+// outside the cutoff, and the warp would take the branch anyway).  A lane's
+// pair enters only when its bit of the entry's member mask is set (the pair
+// lies within r_l; the mask also leaves out slots beyond a cluster's size and
+// the pairs of the base cluster with itself that a list does not own); the
+// others enter as a zero difference, which the rule 0 < R^2 excludes.
 #pragma once
 #include "ljgb_internal.cuh"
 
@@ -35,6 +36,7 @@ struct VclArgs {
   const uint4* pos;
   const uint32_t* cl_start;
   const uint32_t* nbr;  // [ncl][cap], (begin << 3) | (size - 1)
+  const uint64_t* mask; // [ncl][cap], member pairs within r_l: bit a * M + b
   const int32_t* nn;
   int64_t ncl;
   int cap;
@@ -74,18 +76,20 @@ __global__ void __launch_bounds__(256) k_vcl_tile(LJParams P, VclArgs A, ForceOu
     const uint4 pi = A.pos[vi ? i : ib];
     const uint32_t slots = (uint32_t)A.nn[I] * (uint32_t)M;
     const uint32_t* __restrict__ row = A.nbr + I * A.cap;
+    const uint64_t* __restrict__ mrow = A.mask + I * A.cap;
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
 #pragma unroll 2
     for (uint32_t q0 = 0; q0 < slots; q0 += JP) {
       const uint32_t q = q0 + (uint32_t)js;
       const bool vq = act && q < slots;
       uint32_t ent = vq ? row[q / M] : ib << 3;  // a slot past the list reads the base cluster
+      const uint64_t mk = vq ? mrow[q / M] : 0ull;
       if (!LJ_IDX_OK((ent >> 3) + (ent & 7u) < (uint32_t)P.n, out.status)) ent = ib << 3;
       const uint32_t jb = ent >> 3, jj = q % M;
       const bool vj = vq && jj <= (ent & 7u);
       const uint32_t j = jb + jj;
       const uint4 pj = A.pos[vj ? j : jb];
-      const bool ok = vi && vj && (!N3 || jb != ib || j > i);
+      const bool ok = vi && vj && ((mk >> ((uint32_t)ii * M + jj)) & 1ull);
       const int a = ok ? mimg(pi.x, pj.x) : 0, b = ok ? mimg(pi.y, pj.y) : 0, c = ok ? mimg(pi.z, pj.z) : 0;
       R af, bf, cf;
       const R fac = Prec<R>::template pair<EV, false, true>(a, b, c, P, af, bf, cf, eu, ew, cnt);
@@ -158,22 +162,24 @@ __global__ void __launch_bounds__(256) k_vcl_jlane(LJParams P, VclArgs A, ForceO
     for (int k = 0; k < M; ++k) fi[k][0] = fi[k][1] = fi[k][2] = (R)0;
     const uint32_t slots = (uint32_t)A.nn[I] * (uint32_t)M;
     const uint32_t* __restrict__ row = A.nbr + I * A.cap;
+    const uint64_t* __restrict__ mrow = A.mask + I * A.cap;
     R eu = 0, ew = 0;
 #pragma unroll 1
     for (uint32_t q0 = 0; q0 < slots; q0 += 32) {
       const uint32_t q = q0 + (uint32_t)lane;
       const bool vq = q < slots;
       uint32_t ent = vq ? row[q / M] : ib << 3;  // a slot past the list reads the base cluster
+      const uint64_t mk = vq ? mrow[q / M] : 0ull;
       if (!LJ_IDX_OK((ent >> 3) + (ent & 7u) < (uint32_t)P.n, out.status)) ent = ib << 3;
       const uint32_t jb = ent >> 3, jj = q % M;
       const bool vj = vq && jj <= (ent & 7u);
       const uint32_t j = jb + jj;
       const uint4 pj = A.pos[vj ? j : jb];
-      const bool self = jb == ib;
+      const uint64_t mj = vj ? mk >> jj : 0ull;  // bit k * M: this lane's pair with the k-th i
       R gx = 0, gy = 0, gz = 0;
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        const bool ok = vj && (uint32_t)k < ni && (!N3 || !self || (uint32_t)k < jj);
+        const bool ok = (uint32_t)k < ni && ((mj >> (k * M)) & 1ull);
         const int a = ok ? mimg(pi[k].x, pj.x) : 0, b = ok ? mimg(pi[k].y, pj.y) : 0,
                   c = ok ? mimg(pi[k].z, pj.z) : 0;
         R af, bf, cf;
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(256) k_vcl_jlane(LJParams P, VclArgs A, ForceO
 
 template <typename R, bool N3, bool EV>
 cudaError_t vcl_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
-  VclArgs A{c.pos, c.cl_start, c.vcl_nbr, c.vcl_nn, c.vcl_ncl, c.vcl_cap};
+  VclArgs A{c.pos, c.cl_start, c.vcl_nbr, c.vcl_mask, c.vcl_nn, c.vcl_ncl, c.vcl_cap};
   const int64_t threads = std::max<int64_t>(32, c.vcl_ncl * 32);
   const unsigned g = (unsigned)std::min<int64_t>((threads + 255) / 256, 152 * 16);
   const bool tile = cfg.order == LJ_ORD_CL_TILE;

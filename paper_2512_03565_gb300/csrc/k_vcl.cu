@@ -20,8 +20,17 @@
 // within r_l of I's box and, in each, the z-window of clusters found by
 // binary search; one warp per i-cluster appends with ballots.
 //
+// Member masks (reading R21).  A cluster pair found by the box test is kept
+// only if some member pair (a-th particle of I, b-th of J, two different
+// particles; for a half list's J = I only b > a) lies within r_l in the same
+// exact integer rule, and its entry carries the mask of those member pairs,
+// bit a * M + b.  The force kernels take a lane's pair only when its bit is
+// set, and about a fifth of the box-test survivors (clusters of 4 at density
+// 0.75) have an empty mask and are not listed at all.
+//
 // A list entry packs the j-cluster's first particle and its size:
-// (begin << 3) | (size - 1), so the force kernels read one word per cluster.
+// (begin << 3) | (size - 1), so the force kernels read one word per cluster,
+// and its mask is a parallel 64-bit word.
 #include "ljgb_internal.cuh"
 
 namespace ljgb {
@@ -158,6 +167,7 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__
 }
 
 struct VclBuildArgs {
+  const uint4* pos;
   const uint32_t* cl_start;
   const uint4* lo;
   const uint4* hi;
@@ -169,11 +179,32 @@ struct VclBuildArgs {
   uint64_t Rl2;
   uint32_t Rl;           // floor(sqrt(Rl2))
   int cap;
+  int M;                 // cluster size (bit a * M + b of a mask)
   uint32_t* nbr;
+  uint64_t* mask;
   int32_t* nn;
   uint32_t* maxlen;
   uint32_t* status;
 };
+
+// Mask of the member pairs of clusters I and J within r_l (exact integer
+// rule); for J = I only the pairs b > a (half lists) or b != a (full lists).
+template <bool HALF>
+__device__ __forceinline__ uint64_t member_mask(const VclBuildArgs& A, uint32_t I, uint32_t J) {
+  const uint32_t ib = A.cl_start[I], ni = A.cl_start[I + 1] - ib;
+  const uint32_t jb = A.cl_start[J], nj = A.cl_start[J + 1] - jb;
+  uint64_t m = 0;
+  for (uint32_t b = 0; b < nj; ++b) {
+    const uint4 q = A.pos[jb + b];
+    for (uint32_t a = 0; a < ni; ++a) {
+      if (J == I && (HALF ? b <= a : b == a)) continue;
+      const uint4 p = A.pos[ib + a];
+      if (in_cut_exact((int)(q.x - p.x), (int)(q.y - p.y), (int)(q.z - p.z), A.Rl2))
+        m |= 1ull << (a * (uint32_t)A.M + b);
+    }
+  }
+  return m;
+}
 
 // Cluster ranges of tower t whose z interval meets [zl - R, zh + R]
 // (periodic): up to two index ranges [s1, e1) and [s2, e2).
@@ -253,6 +284,7 @@ __global__ void __launch_bounds__(256) k_vcl_build(VclBuildArgs A) {
         const uint32_t o_s2 = __shfl_sync(0xffffffffu, s2, owner);
         bool take = false;
         uint32_t J = 0;
+        uint64_t mk = 0;
         if (k < total) {
           const uint32_t r = k - o_ex;
           J = r < o_l1 ? o_s1 + r : o_s2 + (r - o_l1);
@@ -261,7 +293,10 @@ __global__ void __launch_bounds__(256) k_vcl_build(VclBuildArgs A) {
             const uint64_t dx = ivgap(li.x, hi.x, lj.x, hj.x);
             const uint64_t dy = ivgap(li.y, hi.y, lj.y, hj.y);
             const uint64_t dz = ivgap(li.z, hi.z, lj.z, hj.z);
-            take = dx * dx + dy * dy + dz * dz <= A.Rl2;
+            if (dx * dx + dy * dy + dz * dz <= A.Rl2) {
+              mk = member_mask<HALF>(A, (uint32_t)I, J);
+              take = mk != 0ull;
+            }
           }
         }
         const unsigned m = __ballot_sync(0xffffffffu, take);
@@ -270,6 +305,7 @@ __global__ void __launch_bounds__(256) k_vcl_build(VclBuildArgs A) {
           if (p < (uint32_t)A.cap) {
             const uint32_t jb = A.cl_start[J], je = A.cl_start[J + 1];
             A.nbr[(int64_t)I * A.cap + p] = (jb << 3) | (je - jb - 1u);
+            A.mask[(int64_t)I * A.cap + p] = mk;
           }
         }
         count += (uint32_t)__popc(m);
@@ -379,7 +415,10 @@ cudaError_t launch_vcl_build(Ctx& c, int half, uint32_t* maxlen) {
   while ((r + 1) * (r + 1) <= c.Rl2) ++r;
   A.Rl = (uint32_t)std::min<uint64_t>(r, 0xffffffffull);
   A.cap = c.vcl_cap;
+  A.M = c.vcl_M;
+  A.pos = c.pos;
   A.nbr = c.vcl_nbr;
+  A.mask = c.vcl_mask;
   A.nn = c.vcl_nn;
   A.maxlen = maxlen;
   A.status = c.status;

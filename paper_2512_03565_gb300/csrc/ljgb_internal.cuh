@@ -377,7 +377,7 @@ struct Ctx {
   // Verlet cluster lists (k_vcl.cu): cluster order for cluster size vcl_M,
   // clusters [cl_start[c], cl_start[c+1]) with boxes cl_lo / cl_hi, and the
   // row-major cluster-pair lists [ncl][vcl_cap] of packed entries
-  // (begin << 3) | (size - 1)
+  // (begin << 3) | (size - 1) with their member masks
   int vcl_M = 0;
   int vcl_nt = 0;               // towers per axis
   int64_t vcl_ncl = 0;
@@ -394,6 +394,7 @@ struct Ctx {
   uint32_t* cl_z = nullptr;     // zmin of every cluster, then zmax
   size_t cl_z_cap = 0;
   uint32_t* vcl_nbr = nullptr;
+  uint64_t* vcl_mask = nullptr;  // [ncl][cap]: member pairs within r_l, bit a * M + b
   int32_t* vcl_nn = nullptr;
   int vcl_cap = 0;
   size_t vcl_nbr_cap = 0, vcl_nn_cap = 0;

@@ -29,6 +29,16 @@
   backward half shell (the two roles a cell can take in a cell pair, Sec.
   5.1) on homogeneous, slab and solid systems, in both pair precisions.
 
+* ``precision``: the FP32-pair error of every configuration against the FP64
+  oracle (max |dF| / RMS |F|) on the densest workloads (FCC at 1.2 and 1.0,
+  the fluid at 0.75, a gas at 0.1), with the lengths over which a lane sums
+  in FP32 (list entries and linked-cell candidates per particle).
+
+* ``force-launch``: a few force evaluations of one configuration on the
+  homogeneous fluid (density 0.75, r_c 2.5, skin 0.3) after a warm-up one,
+  for kernel profilers; ``mlp-launch``: one forward and one gradient pass of
+  the tuner network on a batch of rows.
+
 Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy|traversal|clusters
        [options]
 """
@@ -293,29 +303,65 @@ def clusters(samples=5, evals=20, log=print):
                 d.compute_forces(cfg)
             ms, n, _ = d.timing(0)
             kernel[lj.config_name(cfg)] = ms / max(n, 1)
-        cand = {}
+        cand, masked = {}, {}
         for M in (4, 6, 8):
             d.build_clusters(M, 0)
             cs, _ = d.clusters()
             sizes = np.diff(cs).astype(np.int64)
             lists = d.cluster_lists()
             cand[M] = float(sum(sizes[I] * sizes[l].sum() for I, l in enumerate(lists)) / s.n)
+            bits = sum(int(sum(bin(int(v)).count("1") for v in m)) for m in d.cluster_masks())
+            masked[M] = float(bits / s.n)
         d.build_verlet(0)
         _, nn = d.verlet()
         r = {"system": s.name, "n": s.n, "best_vl": best_vl, "times_ms": times, "kernel_ms": kernel,
-             "cluster_candidates_per_particle": cand, "verlet_entries_per_particle": float(nn.mean())}
+             "cluster_candidates_per_particle": cand, "masked_pairs_per_particle": masked,
+             "verlet_entries_per_particle": float(nn.mean())}
         out.append(r)
         vcl = {k: v for k, v in kernel.items() if k.startswith("VCL:")}
         bv = min(vcl, key=vcl.get)
         log(f"{s.name}: VL {best_vl} kernel {kernel[best_vl]:.4f} ms; best VCL {bv} {vcl[bv]:.4f} ms; "
-            f"candidates/particle {cand} vs VL entries {nn.mean():.1f}")
+            f"candidates/particle {cand}, masked pairs/particle {masked} vs VL entries {nn.mean():.1f}")
+    return out
+
+
+def precision(n=8000, log=print):
+    import oracle
+    oracle.build()
+    systems = [W.fcc(n, 1.2, 71), W.fcc(n, 1.0, 72), W.stratified(n, 0.75, 73), W.stratified(n, 0.1, 74)]
+    out = []
+    for s in systems:
+        F_ref, _, _, np_ref = oracle.forces_bruteforce(s.pos, s.L, s.rc)
+        rms = float(np.sqrt((F_ref ** 2).sum(0).mean()))
+        d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP32_ACC64)
+        d.set_particles(s.pos, s.vel)
+        errs = {}
+        for cfg in lj.configs():
+            d.compute_forces(cfg)
+            errs[lj.config_name(cfg)] = float(np.abs(d.forces() - F_ref).max() / rms)
+        d.build_verlet(0)
+        _, nn = d.verlet()
+        d.close()
+        rho = s.n / s.L ** 3
+        nc = int(s.L // s.rc)
+        cand = 27.0 * s.n / nc ** 3
+        worst = max(errs, key=errs.get)
+        r = {"system": s.name, "n": s.n, "rho": rho, "pairs_in_cutoff_per_particle": 2.0 * np_ref / s.n,
+             "verlet_entries_per_particle_mean": float(nn.mean()), "verlet_entries_max": int(nn.max()),
+             "lc_candidates_per_particle": cand, "rms_force": rms, "worst_config": worst,
+             "worst_err": errs[worst], "errors": errs}
+        log(f"{s.name}: worst {worst} {errs[worst]:.3e}; list mean {nn.mean():.1f} max {nn.max()}")
+        out.append(r)
     return out
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy",
-                                     "traversal", "clusters"])
+                                     "traversal", "clusters", "force-launch", "mlp-launch", "precision"])
+    ap.add_argument("--cfg", default="1,3,4,0", help="force-launch: container,order,param,newton3")
+    ap.add_argument("--particles", type=int, default=524288)
+    ap.add_argument("--evals", type=int, default=3)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--data", default="tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
@@ -362,6 +408,34 @@ def main(argv=None):
         ens.run(0.002, a.steps, use_graph=False)
         print(json.dumps({"steps": a.steps, "ms_per_step": (time.perf_counter() - t0) / max(1, a.steps) * 1e3}))
         ens.close()
+    elif a.what == "precision":
+        res = precision()
+        print(json.dumps([{k: v for k, v in r.items() if k != "errors"} for r in res]))
+        if a.out:
+            json.dump(res, open(a.out, "w"))
+    elif a.what == "force-launch":
+        s = W.homogeneous(a.particles, 0.75, W.BASE_SEED + 1, T=1.0, rc=2.5, skin=0.3)
+        cfg = lj.config(*[int(v) for v in a.cfg.split(",")])
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos, s.vel)
+        d.compute_forces(cfg)
+        d.timing(1)
+        for _ in range(a.evals):
+            d.compute_forces(cfg)
+        ms, k, _ = d.timing(0)
+        print(json.dumps({"config": lj.config_name(cfg), "n": s.n, "evals": a.evals,
+                          "force_kernel_ms": ms / max(k, 1)}))
+        d.close()
+    elif a.what == "mlp-launch":
+        model = tuner.load()
+        rng = np.random.default_rng(5)
+        X = rng.standard_normal((4096, 16)).astype(np.float32)
+        C_out = int(model["C"])
+        T = rng.standard_normal((4096, C_out)).astype(np.float32)
+        M = np.ones_like(T)
+        lj.mlp_forward(model["params"], C_out, X)
+        lj.mlp_loss_grad(model["params"], C_out, X, T, M)
+        print(json.dumps({"rows": 4096, "outputs": C_out}))
     elif a.what == "clusters":
         res = clusters()
         if a.out:

@@ -80,6 +80,7 @@ _SIGS = {
     "lj_build_clusters": (C.c_int, [_VP, C.c_int32, C.c_int32]),
     "lj_get_clusters": (C.c_int, [_VP, C.POINTER(C.c_int64), _VP, C.POINTER(C.c_int32)]),
     "lj_get_cluster_lists": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int32)]),
+    "lj_get_cluster_masks": (C.c_int, [_VP, _VP]),
     "lj_compute_forces": (C.c_int, [_VP, lj_config, _VP, _VP]),
     "lj_config_valid": (C.c_int32, [lj_config]),
     "lj_config_list": (C.c_int32, [_VP, C.c_int32]),
@@ -337,6 +338,18 @@ class Domain:
         self._check(self.lib.lj_get_cluster_lists(self.h, nbr.ctypes.data, nn.ctypes.data, C.byref(cap)))
         return [nbr[I, :nn[I]].copy() for I in range(ncl)]
 
+
+    def cluster_masks(self):
+        """Member masks of the cluster-pair lists (a list of uint64 arrays, in
+        the order of cluster_lists)."""
+        cap = C.c_int32()
+        ncl = C.c_int64()
+        self._check(self.lib.lj_get_clusters(self.h, C.byref(ncl), None, None))
+        nn = np.zeros(max(ncl.value, 1), dtype=np.int32)
+        self._check(self.lib.lj_get_cluster_lists(self.h, None, nn.ctypes.data, C.byref(cap)))
+        m = np.zeros((max(ncl.value, 1), max(cap.value, 1)), dtype=np.uint64)
+        self._check(self.lib.lj_get_cluster_masks(self.h, m.ctypes.data))
+        return [m[I, :nn[I]].copy() for I in range(ncl.value)]
     def counters(self):
         c = np.zeros(5, dtype=np.int64)
         self._check(self.lib.lj_get_counters(self.h, c.ctypes.data))

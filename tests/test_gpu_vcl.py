@@ -1,10 +1,11 @@
 """Verlet cluster lists on the GPU against the oracle (Sec. 2.1.1's cluster
 container; cluster sizes 4, 6 and 8 of Sec. 5.1).
 
-The cluster order, the cluster boundaries and the cluster-pair lists are
-integer results decided by exact integer rules: the order and boundaries are
-compared bit for bit, the lists as sets per cluster (the library's search
-order is not defined).  Forces of every cluster configuration are compared
+The cluster order, the cluster boundaries, the cluster-pair lists and their
+member masks are integer results decided by exact integer rules: the order
+and boundaries are compared bit for bit, the lists as sets per cluster (the
+library's search order is not defined) and each entry's mask with the
+oracle's mask of the same cluster pair.  Forces of every cluster configuration are compared
 with the brute force in the force-parity tests (they iterate over all
 configurations); here also across rebuilds, capacity regrowth and the
 full-size fluid on sampled particles."""
@@ -54,11 +55,12 @@ def test_cluster_order_and_lists_bit_exact(lj, M, half):
         perm, _, nt = d.cells()
         cs, nt2 = d.clusters()
         lists = d.cluster_lists()
+        masks = d.cluster_masks()
         vcl_pairs = d.pairs(lj.LJ_VCL)
         d.close()
         # the member pairs within r_l of the listed cluster pairs are exactly the brute-force r_l pairs
         assert np.array_equal(vcl_pairs, oracle.pairs_bruteforce(pos, L, rc + skin)), name
-        perm_ref, cs_ref, lists_ref = oracle.vcl_lists(pos, L, rc + skin, M, half)
+        perm_ref, cs_ref, lists_ref, masks_ref = oracle.vcl_lists(pos, L, rc + skin, M, half, masks=True)
         assert nt == nt2 == oracle.vcl_ntower(pos.shape[1], M), name
         assert np.array_equal(perm, perm_ref), name
         assert np.array_equal(cs, cs_ref), name
@@ -66,6 +68,8 @@ def test_cluster_order_and_lists_bit_exact(lj, M, half):
         for I, (got, ref) in enumerate(zip(lists, lists_ref)):
             assert len(set(got.tolist())) == len(got), (name, I)
             assert sorted(got.tolist()) == ref.tolist(), (name, I)
+            want = {int(J): int(m) for J, m in zip(ref, masks_ref[I])}
+            assert {int(J): int(m) for J, m in zip(got, masks[I])} == want, (name, I)
 
 
 def test_lists_follow_the_particles_across_rebuilds(lj):

@@ -338,57 +338,65 @@ def _clusters_of(perm, cls, n):
 
 
 def test_vcl_lists_with_singleton_clusters_are_verlet_lists(orc):
-    """M = 1: every box is a point and D^2 is the pair's R^2, so the cluster
-    lists are the particle Verlet lists (plus the particle itself)."""
+    """M = 1: a cluster is one particle and its only member pair with J is
+    the particle pair, so the cluster lists are the particle Verlet lists
+    (pairs at zero separation excluded, no particle lists itself)."""
     for name, L, pos in vcl_cases()[:6]:
         n, rl = pos.shape[1], 1.0
-        perm, cls, lists = orc.vcl_lists(pos, L, rl, 1, 0)
+        perm, cls, lists, masks = orc.vcl_lists(pos, L, rl, 1, 0, masks=True)
         cl = _clusters_of(perm, cls, n)
         want = [set() for _ in range(n)]
-        for i in range(n):
-            want[cl[i]].add(int(cl[i]))
         for i, j in orc.pairs_bruteforce(pos, L, rl):
-            want[cl[i]].add(int(cl[j]))
-            want[cl[j]].add(int(cl[i]))
-        zero = [(i, j) for i in range(n) for j in range(i + 1, n) if orc.r2_int(pos[:, i], pos[:, j]) == 0]
-        for i, j in zero:
             want[cl[i]].add(int(cl[j]))
             want[cl[j]].add(int(cl[i]))
         got = [set(int(v) for v in lists[c]) for c in range(n)]
         assert got == [want[c] for c in range(n)], name
+        assert all(np.all(m == 1) for m in masks), name
 
 
 @pytest.mark.parametrize("M", [4, 6, 8])
-def test_vcl_lists_cover_every_pair_and_stay_near(orc, M):
-    """Every pair within r_l lands in a listed cluster pair; every listed pair
-    has two members within r_l plus both boxes' diagonals; full lists are
-    symmetric and half lists are the full ones with J >= I."""
+def test_vcl_lists_and_masks_are_the_member_pairs_within_rl(orc, M):
+    """Against the brute-force r_l pair set, independently of the cluster
+    search: the listed cluster pairs of the full lists are exactly the
+    cluster pairs of the brute-force pairs (both directions), and the mask
+    bits of the listed pairs, mapped back to particles, are exactly those
+    pairs; half lists hold each pair once (J > I, or J = I with b > a) and
+    are the full lists' entries with J >= I."""
     for name, L, pos in vcl_cases():
         n = pos.shape[1]
         rl = 1.0 if L < 7 else 2.8
-        perm, cls, full = orc.vcl_lists(pos, L, rl, M, 0)
-        _, _, half = orc.vcl_lists(pos, L, rl, M, 1)
+        perm, cls, full, fmask = orc.vcl_lists(pos, L, rl, M, 0, masks=True)
+        _, _, half, hmask = orc.vcl_lists(pos, L, rl, M, 1, masks=True)
         ncl = len(cls) - 1
         cl = _clusters_of(perm, cls, n)
-        fs = [set(int(v) for v in full[c]) for c in range(ncl)]
+        rank = np.empty(n, dtype=np.int64)
+        for c in range(ncl):
+            rank[perm[cls[c]:cls[c + 1]]] = np.arange(cls[c + 1] - cls[c])
+        bf = {(int(i), int(j)) for i, j in orc.pairs_bruteforce(pos, L, rl)}
+        want_full = {(int(cl[i]), int(cl[j])) for i, j in bf} | {(int(cl[j]), int(cl[i])) for i, j in bf}
+        got_full = {(I, int(J)) for I in range(ncl) for J in full[I]}
+        assert got_full == want_full, name
+        assert all(list(full[I]) == sorted(full[I]) for I in range(ncl)), name
+        pairs_full, pairs_half = set(), []
         for I in range(ncl):
-            assert list(full[I]) == sorted(fs[I]) and I in fs[I], name
-            assert set(int(v) for v in half[I]) == {J for J in fs[I] if J >= I}, name
-            for J in fs[I]:
-                assert I in fs[J], name
-        for i, j in orc.pairs_bruteforce(pos, L, rl):
-            assert int(cl[j]) in fs[cl[i]], name
-        u = L / TWO32
-        lo = np.array([pos[:, perm[cls[c]:cls[c + 1]]].min(axis=1) for c in range(ncl)], dtype=np.float64)
-        hi = np.array([pos[:, perm[cls[c]:cls[c + 1]]].max(axis=1) for c in range(ncl)], dtype=np.float64)
-        diag = np.sqrt(((hi - lo) ** 2).sum(axis=1)) * u
-        rng = np.random.default_rng(5)
-        for I in rng.choice(ncl, size=min(ncl, 40), replace=False):
             mi = perm[cls[I]:cls[I + 1]]
-            for J in fs[I]:
+            for J, m in zip(full[I], fmask[I]):
                 mj = perm[cls[J]:cls[J + 1]]
-                d = min(math.sqrt(orc.r2_int(pos[:, a], pos[:, b])) * u for a in mi for b in mj)
-                assert d <= rl + diag[I] + diag[J] + 1e-9, name
+                for a in range(len(mi)):
+                    for b in range(len(mj)):
+                        if (int(m) >> (a * M + b)) & 1:
+                            pairs_full.add((min(mi[a], mj[b]), max(mi[a], mj[b])))
+            for J, m in zip(half[I], hmask[I]):
+                assert J >= I and m != 0, name
+                mj = perm[cls[J]:cls[J + 1]]
+                for a in range(len(mi)):
+                    for b in range(len(mj)):
+                        if (int(m) >> (a * M + b)) & 1:
+                            assert J > I or b > a, name
+                            pairs_half.append((min(mi[a], mj[b]), max(mi[a], mj[b])))
+            assert [int(J) for J in half[I]] == [int(J) for J in full[I] if J >= I], name
+        assert pairs_full == bf, name
+        assert len(pairs_half) == len(bf) and set(pairs_half) == bf, name
 
 
 # --- integrator ----------------------------------------------------------------
