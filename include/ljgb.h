@@ -68,8 +68,13 @@ typedef enum { LJ_PREC_FP64 = 0, LJ_PREC_FP32_ACC64 = 1 } lj_precision;
  * Verlet cluster lists: clusters of M particles (M = 4, 6 or 8, the cluster
  * sizes of Sec. 5.1) with lists of whole neighbour clusters within r_c + skin
  * (see lj_build_clusters).  Both list containers are rebuilt every few steps
- * and whenever a particle has moved more than skin/2 since the build. */
-typedef enum { LJ_LC = 0, LJ_VL = 1, LJ_VCL = 2 } lj_container;
+ * and whenever a particle has moved more than skin/2 since the build.
+ * LJ_LCS is linked cells of edge >= r_c / 2 (sub-cells; the paper's cells of
+ * edge = cutoff are its special case of edge r_c): a particle visits the
+ * 5 x 5 x 5 cells around its own, which hold a quarter of the 27-cell
+ * candidates' volume, so about twice the fraction of candidates lies inside
+ * r_c.  It needs at least 5 cells per axis and runs the JSPLIT order only. */
+typedef enum { LJ_LC = 0, LJ_VL = 1, LJ_VCL = 2, LJ_LCS = 3 } lj_container;
 
 /* Interaction orders: the GPU analogues of the paper's register-filling
  * patterns (Sec. 4.1.1, Fig. 4).
@@ -151,10 +156,11 @@ lj_status lj_set_particles_fp(lj_ctx* ctx, int64_t n, const uint32_t* pos_fp, co
 lj_status lj_update_positions(lj_ctx* ctx, const double* pos, int32_t on_device);
 
 /* Bin the particles into the cells of one container by a stable counting sort
- * on the cell id (Sec. 2.1.1, Linked Cells): cells of edge >= r_c (LJ_LC) or
- * >= r_c + skin (LJ_VL), n_c = floor(L / edge) per axis, at least 3.  The
+ * on the cell id (Sec. 2.1.1, Linked Cells): cells of edge >= r_c (LJ_LC),
+ * >= r_c / 2 (LJ_LCS) or >= r_c + skin (LJ_VL), n_c = floor(L / edge) per
+ * axis, at least 3 (5 for LJ_LCS).  The
  * library's particle storage is reordered to cell order (ties keep ascending
- * original index).  Errors: LJ_ERR_STATE, LJ_ERR_ARG (n_c < 3), LJ_ERR_CUDA. */
+ * original index).  Errors: LJ_ERR_STATE, LJ_ERR_ARG (too few cells), LJ_ERR_CUDA. */
 lj_status lj_bin_cells(lj_ctx* ctx, int32_t container);
 
 /* Build Verlet lists (Sec. 2.1.1) on the r_c + skin cells: every j != i within

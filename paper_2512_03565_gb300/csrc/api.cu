@@ -95,6 +95,10 @@ bool order_is_valid(const lj_config& g) {
     }
     return g.newton3 == LJ_N3_OFF || g.newton3 == LJ_N3_ATOMIC || g.newton3 == LJ_N3_ATOMIC_BWD;
   }
+  if (g.container == LJ_LCS) {
+    if (g.order != LJ_ORD_JSPLIT || (g.param != 8 && g.param != 4 && g.param != 2)) return false;
+    return g.newton3 == LJ_N3_OFF || g.newton3 == LJ_N3_ATOMIC || g.newton3 == LJ_N3_ATOMIC_BWD;
+  }
   if (g.container == LJ_VCL) {
     if (g.order != LJ_ORD_CL_TILE && g.order != LJ_ORD_CL_JLANE) return false;
     if (g.param != 4 && g.param != 6 && g.param != 8) return false;
@@ -137,6 +141,9 @@ std::vector<lj_config> all_configs() {
   for (int n3 : n3s)
     for (int ord : {LJ_ORD_CL_TILE, LJ_ORD_CL_JLANE})
       for (int m : {4, 6, 8}) v.push_back({LJ_VCL, ord, m, n3});
+  // linked cells of edge >= r_c / 2 (sub-cells), JSPLIT x Newton-3 (forward and backward half)
+  for (int n3 : {LJ_N3_OFF, LJ_N3_ATOMIC, LJ_N3_ATOMIC_BWD})
+    for (int w : {8, 4, 2}) v.push_back({LJ_LCS, LJ_ORD_JSPLIT, w, n3});
   return v;
 }
 
@@ -202,10 +209,11 @@ void reset_state_flags(Ctx& c) {
 }
 
 lj_status do_bin(Ctx& c, int container) {
-  const int nc = container == LJ_LC ? c.nc_lc : c.nc_vl;
-  if (nc < 3)
-    return fail(c, LJ_ERR_ARG, "box holds fewer than 3 cells per axis for this container (edge " +
-                                   std::to_string(c.L / 3) + ")");
+  const int nc = container == LJ_LC ? c.nc_lc : container == LJ_LCS ? c.nc_lcs : c.nc_vl;
+  const int need = container == LJ_LCS ? 5 : 3;
+  if (nc < need)
+    return fail(c, LJ_ERR_ARG, "box holds fewer than " + std::to_string(need) +
+                                   " cells per axis for this container (edge " + std::to_string(c.L / need) + ")");
   c.P.nc = nc;
   CK(bin_cells(c, nc));
   c.launches += 7;  // cell ids, 3 scan passes, scatter, per-cell sort, permute
@@ -405,9 +413,9 @@ lj_status list_is_fresh(Ctx& c, bool& fresh) {
 // Makes the container structures current for cfg.
 lj_status prepare(Ctx& c, const lj_config& cfg, bool allow_rebuild_schedule) {
   (void)allow_rebuild_schedule;
-  if (cfg.container == LJ_LC) {
-    if (c.binned_for != LJ_LC || c.moved) CKS(do_bin(c, LJ_LC));
-    c.P.nc = c.nc_lc;
+  if (cfg.container == LJ_LC || cfg.container == LJ_LCS) {
+    if (c.binned_for != cfg.container || c.moved) CKS(do_bin(c, cfg.container));
+    c.P.nc = cfg.container == LJ_LC ? c.nc_lc : c.nc_lcs;
     return LJ_OK;
   }
   bool fresh = false;
@@ -466,7 +474,7 @@ lj_status run_force(Ctx& c, const lj_config& cfg, bool ev, bool acc_zeroed = fal
     CK(build_tiles(c, T));
   }
   if (t0) CK(cudaEventRecord(t0, c.stream));
-  if (cfg.container == LJ_LC)
+  if (cfg.container == LJ_LC || cfg.container == LJ_LCS)
     e = f64 ? force_lc_f64(c, cfg, ev) : force_lc_f32(c, cfg, ev);
   else if (cfg.container == LJ_VCL)
     e = f64 ? force_vcl_f64(c, cfg, ev) : force_vcl_f32(c, cfg, ev);
@@ -556,6 +564,7 @@ lj_status lj_init_domain(lj_ctx** out, const double box[3], double cutoff, doubl
   c.stream = (cudaStream_t)cuda_stream;
   c.nc_lc = (int)std::floor(L / cutoff);
   c.nc_vl = (int)std::floor(L / (cutoff + skin));
+  c.nc_lcs = (int)std::floor(L / (0.5 * cutoff));
   const double u = std::ldexp(L, -32);
   LJParams& P = c.P;
   P.Rc2 = exact_cut2(L, cutoff);
@@ -717,7 +726,8 @@ lj_status lj_bin_cells(lj_ctx* h, int32_t container) {
   if (!h) return LJ_ERR_ARG;
   Ctx& c = h->c;
   CKS(need_particles(c));
-  if (container != LJ_LC && container != LJ_VL) return fail(c, LJ_ERR_ARG, "unknown container");
+  if (container != LJ_LC && container != LJ_VL && container != LJ_LCS)
+    return fail(c, LJ_ERR_ARG, "unknown container");
   CKS(do_bin(c, container));
   CK(cudaGetLastError());
   return LJ_OK;
@@ -822,7 +832,7 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
   if (!(dt > 0) || nsteps < 0 || rebuild_every < 1) return fail(c, LJ_ERR_ARG, "need dt > 0, nsteps >= 0, rebuild_every >= 1");
   const double hdtm = 0.5 * dt / c.mass;
   const double dtu = dt * 4294967296.0 / c.L;
-  const bool vl = cfg.container != LJ_LC;  // a list container
+  const bool vl = cfg.container == LJ_VL || cfg.container == LJ_VCL;  // a list container
   c.skin_pending = false;  // the steps below check the skin themselves
   if (!c.forces_valid || memcmp(&c.last_cfg, &cfg, sizeof(cfg)) != 0) {
     CKS(prepare(c, cfg, false));
@@ -868,8 +878,8 @@ lj_status lj_integrate_step(lj_ctx* h, double dt, int32_t nsteps, int32_t rebuil
         CKS(run_force(c, cfg, false));
       }
     } else {
-      CKS(do_bin(c, LJ_LC));
-      c.P.nc = c.nc_lc;
+      CKS(do_bin(c, cfg.container));
+      c.P.nc = cfg.container == LJ_LCS ? c.nc_lcs : c.nc_lc;
       CKS(run_force(c, cfg, false));
     }
     c.kick_pending = true;

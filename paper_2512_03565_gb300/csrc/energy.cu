@@ -151,7 +151,10 @@ lj_status lj_tune_energy(lj_ctx* ctx, double min_ms, lj_config* chosen, double* 
   double best_mj = std::numeric_limits<double>::infinity();
   for (size_t k = 0; k < all.size() && st == LJ_OK; ++k) {
     const lj_config& g = all[k];
-    if (!lj_config_valid(g) || (g.container == LJ_LC ? c.nc_lc < 3 : g.container == LJ_VL && c.nc_vl < 3)) continue;
+    if (!lj_config_valid(g) || (g.container == LJ_LC    ? c.nc_lc < 3
+                                : g.container == LJ_LCS ? c.nc_lcs < 5
+                                                        : g.container == LJ_VL && c.nc_vl < 3))
+      continue;
     // warm-up (builds the lists or bins), then one timed evaluation sizes the batch
     if ((st = lj_compute_forces(ctx, g, nullptr, nullptr)) != LJ_OK) break;
     cudaEventRecord(e0, c.stream);
@@ -182,8 +185,9 @@ lj_status lj_tune_energy(lj_ctx* ctx, double min_ms, lj_config* chosen, double* 
     const double w0 = now_ms();
     cudaEventRecord(e0, c.stream);
     for (int64_t s = 0; s < evals && st == LJ_OK; ++s) {
-      if (g.container == LJ_LC) c.moved = true;  // a step's rebin is part of the cost
-      if (g.container != LJ_LC && s % per == 0 && s > 0) {
+      const bool cells = g.container == LJ_LC || g.container == LJ_LCS;
+      if (cells) c.moved = true;  // a step's rebin is part of the cost
+      if (!cells && s % per == 0 && s > 0) {
         c.moved_since_build = true;
         c.vl_valid = false;  // the list build of the rebuild period
         c.vcl_valid = false;

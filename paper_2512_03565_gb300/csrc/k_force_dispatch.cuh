@@ -53,6 +53,14 @@ cudaError_t lc_launch(Ctx& c, const lj_config& cfg, ForceOut out) {
     case LJ_ORD_JSPLIT: {
       const int w = cfg.param;
       const int64_t thr = n * w;
+      if (cfg.container == LJ_LCS) {  // sub-cells: the 5 x 5 x 5 stencil
+        switch (w) {
+          case 8: k_lc_jsplit<R, 8, N3, EV, BWD, 2><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+          case 4: k_lc_jsplit<R, 4, N3, EV, BWD, 2><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+          default: k_lc_jsplit<R, 2, N3, EV, BWD, 2><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
+        }
+        break;
+      }
       switch (w) {
         case 32: k_lc_jsplit<R, 32, N3, EV, BWD><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;
         case 16: k_lc_jsplit<R, 16, N3, EV, BWD><<<grid_for(thr, 256, 16), 256, 0, c.stream>>>(c.P, c.pos, c.cell_start, out); break;

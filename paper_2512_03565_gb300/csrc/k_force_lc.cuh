@@ -121,6 +121,62 @@ __device__ __forceinline__ int make_segments(const uint32_t* __restrict__ cs, in
   return ns;
 }
 
+// Segments of one particle i (sorted index i, cell (cx, cy, cz)) on sub-cells of
+// edge >= r_c / 2: the 5 x 5 x 5 cells around its own (nc >= 5, so that the
+// offsets -2..2 name distinct cells on every axis).  Full shell: the 25 rows
+// (dz, dy) in {-2..2}^2 with x-cells cx-2..cx+2.  Forward half (Newton-3): the
+// offsets after (0, 0, 0) in (dz, dy, dx) order, which hold every pair once:
+// the own cell's j > i and the x-cells cx+1, cx+2 of the own row, the rows
+// (0, +1), (0, +2), and the 10 rows with dz = +1, +2.  Backward half: the
+// mirror (j < i, x-cells cx-2, cx-1, rows (0, -1), (0, -2), dz = -1, -2).
+// All segments are of kind 0: the set is this particle's own.
+// Segments of the x-cells lo..hi (any integers with hi - lo < nc, taken modulo
+// nc) in row r: one or two contiguous pieces, the wrapped one first.
+__device__ __forceinline__ int row_segments_mod(const uint32_t* __restrict__ cs, int nc, int r, int lo, int hi,
+                                                Seg* out) {
+  const int64_t base = (int64_t)r * nc;
+  const int len = hi - lo + 1;
+  const int a = ((lo % nc) + nc) % nc;
+  if (a + len <= nc) {
+    out[0] = {cs[base + a], cs[base + a + len], 0};
+    return 1;
+  }
+  out[0] = {cs[base], cs[base + a + len - nc], 0};
+  out[1] = {cs[base + a], cs[base + nc], 0};
+  return 2;
+}
+
+template <bool HALF, bool BWD = false>
+__device__ __forceinline__ int make_segments_sub(const uint32_t* __restrict__ cs, int nc, int cx, int cy, int cz,
+                                                 uint32_t i, Seg* segs) {
+  int ns = 0;
+  auto row_of = [&](int dz, int dy) { return ((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc; };
+  if (!HALF) {
+#pragma unroll 1
+    for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll 1
+      for (int dy = -2; dy <= 2; ++dy) ns += row_segments_mod(cs, nc, row_of(dz, dy), cx - 2, cx + 2, segs + ns);
+    return ns;
+  }
+  const int own = row_of(0, 0);
+  const int64_t base = (int64_t)own * nc;
+  const int s = BWD ? -1 : 1;
+  if (!BWD) {
+    segs[ns++] = {i + 1u, cs[base + cx + 1], 0};                       // own cell, j > i
+    ns += row_segments_mod(cs, nc, own, cx + 1, cx + 2, segs + ns);         // x-cells cx+1, cx+2 (wrapping)
+  } else {
+    segs[ns++] = {cs[base + cx], i, 0};                                 // own cell, j < i
+    ns += row_segments_mod(cs, nc, own, cx - 2, cx - 1, segs + ns);         // x-cells cx-2, cx-1 (wrapping)
+  }
+  ns += row_segments_mod(cs, nc, row_of(0, s), cx - 2, cx + 2, segs + ns);
+  ns += row_segments_mod(cs, nc, row_of(0, 2 * s), cx - 2, cx + 2, segs + ns);
+#pragma unroll 1
+  for (int dz = 1; dz <= 2; ++dz)
+#pragma unroll 1
+    for (int dy = -2; dy <= 2; ++dy) ns += row_segments_mod(cs, nc, row_of(s * dz, dy), cx - 2, cx + 2, segs + ns);
+  return ns;
+}
+
 // Checks build: a segment outside [0, n] (a corrupt cell start) is emptied
 // and reported; in the default build this does nothing.
 __device__ __forceinline__ void check_segs(Seg* segs, int ns, uint32_t n, uint32_t* status) {
@@ -542,7 +598,9 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
 // JSPLIT<W>: groups of W lanes per i (32/W i's per warp, consecutive in cell
 // order); every group walks its own i's 27-cell (or half-shell) segments.
 // ---------------------------------------------------------------------------
-template <typename R, int W, bool N3, bool EV, bool BWD = false>
+// REACH = 2: sub-cells of edge >= r_c / 2, each i walking its own 5 x 5 x 5
+// cells (make_segments_sub).
+template <typename R, int W, bool N3, bool EV, bool BWD = false, int REACH = 1>
 __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __restrict__ pos,
                                                    const uint32_t* __restrict__ cs, ForceOut out) {
   constexpr int G = 32 / W;
@@ -557,11 +615,48 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
     const bool vi = ii < (uint32_t)P.n;
     const uint4 pi = vi ? pos[ii] : make_uint4(0, 0, 0, 0);
     const int cx = (int)cx_of(pi.x, nc), cy = (int)cx_of(pi.y, nc), cz = (int)cx_of(pi.z, nc);
-    Seg segs[18];
-    int ns = vi ? make_segments<N3, BWD>(cs, nc, cz * nc + cy, cx, cx, ii, ii, segs) : 0;
+    Seg segs[REACH == 2 ? 52 : 18];
+    int ns = 0;
+    if (vi) {
+      if (REACH == 2) ns = make_segments_sub<N3, BWD>(cs, nc, cx, cy, cz, ii, segs);
+      else ns = make_segments<N3, BWD>(cs, nc, cz * nc + cy, cx, cx, ii, ii, segs);
+    }
     check_segs(segs, ns, (uint32_t)P.n, out.status);
-    const int nsmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)ns);
     R fx = 0, fy = 0, fz = 0, eu = 0, ew = 0;
+    if (REACH == 2) {
+      // the 25-50 short segments (about 7 particles each) as one packed
+      // stream: lane sub takes positions sub, sub + W, ... with a running
+      // segment pointer, so lanes do not idle at every segment's end
+      uint32_t total = 0;
+      for (int s = 0; s < ns; ++s) total += segs[s].e - segs[s].b;
+      const uint32_t tmax = __reduce_max_sync(0xffffffffu, (total + W - 1) / W);
+      int sl = 0;
+      uint32_t base = 0;
+#pragma unroll 1
+      for (uint32_t q = 0; q < tmax; ++q) {
+        const uint32_t p = q * W + sub;
+        while (sl < ns && p >= base + (segs[sl].e - segs[sl].b)) {
+          base += segs[sl].e - segs[sl].b;
+          ++sl;
+        }
+        if (p < total) {
+          const uint32_t j = segs[sl].b + (p - base);
+          const uint4 pj = pos[j];
+          R af, bf, cf_;
+          const R fac = Prec<R>::template pair<EV, true>(mimg(pi.x, pj.x), mimg(pi.y, pj.y), mimg(pi.z, pj.z), P, af,
+                                                   bf, cf_, eu, ew, cnt);
+          fx += fac * af;
+          fy += fac * bf;
+          fz += fac * cf_;
+          if (N3) {
+            atomic_add_raw(out.fx + j, fac * af);
+            atomic_add_raw(out.fy + j, fac * bf);
+            atomic_add_raw(out.fz + j, fac * cf_);
+          }
+        }
+      }
+    }
+    const int nsmax = REACH == 2 ? 0 : (int)__reduce_max_sync(0xffffffffu, (unsigned)ns);
 #pragma unroll 1
     for (int s = 0; s < nsmax; ++s) {
       const Seg sg = (s < ns) ? segs[s] : Seg{0u, 0u, 0};

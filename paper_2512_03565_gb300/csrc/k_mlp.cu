@@ -114,20 +114,34 @@ __global__ void __launch_bounds__(64) k_mlp_backward_rows(const float* __restric
   }
 }
 
-// gW[o][k] = sum_m D[m][o] A[m][k] (k < K), gb[o] = sum_m D[m][o]; one thread
-// per output entry, rows summed in order.
-__global__ void k_mlp_wgrad(const float* __restrict__ A, int K, const float* __restrict__ D, int O, int64_t M,
-                            float* __restrict__ gW, float* __restrict__ gb) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= O * (K + 1)) return;
-  const int o = t / (K + 1), k = t % (K + 1);
+// gW[o][k] = sum_m D[m][o] A[m][k] (k < K), gb[o] = sum_m D[m][o] (the column
+// k = K).  Block (o, 32-column chunk): lane tx takes column 32 chunk + tx,
+// row group ty the rows m = ty, ty + WG_ROWS, ...; the WG_ROWS partial sums of
+// a column are added in a fixed order in shared memory, so the result does not
+// depend on scheduling.  The row loads of A are coalesced over the columns and
+// D[m][o] is broadcast.
+constexpr int WG_ROWS = 32;
+__global__ void __launch_bounds__(32 * WG_ROWS) k_mlp_wgrad(const float* __restrict__ A, int K,
+                                                           const float* __restrict__ D, int O, int64_t M,
+                                                           float* __restrict__ gW, float* __restrict__ gb) {
+  __shared__ float part[WG_ROWS][33];
+  const int o = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  const int k = blockIdx.y * 32 + tx;
   float s = 0.0f;
-  if (k < K) {
-    for (int64_t m = 0; m < M; ++m) s = fmaf(D[m * O + o], A[m * K + k], s);
-    gW[o * K + k] = s;
-  } else {
-    for (int64_t m = 0; m < M; ++m) s += D[m * O + o];
-    gb[o] = s;
+  if (k <= K) {
+#pragma unroll 4
+    for (int64_t m = ty; m < M; m += WG_ROWS) {
+      const float d = D[m * O + o];
+      s = k < K ? fmaf(d, A[m * K + k], s) : s + d;
+    }
+  }
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && k <= K) {
+    float t = 0.0f;
+    for (int r = 0; r < WG_ROWS; ++r) t += part[r][tx];
+    if (k < K) gW[o * K + k] = t;
+    else gb[o] = t;
   }
 }
 
@@ -219,9 +233,10 @@ static cudaError_t mlp_fwd_bwd(MlpWork& w, cudaStream_t s) {
   float* gb2 = gW2 + MH * MH;
   float* gW3 = gb2 + MH;
   float* gb3 = gW3 + (int64_t)C * MH;
-  k_mlp_wgrad<<<(MH * (MIN_ + 1) + 127) / 128, 128, 0, s>>>(w.X, MIN_, w.D1, MH, M, gW1, gb1);
-  k_mlp_wgrad<<<(MH * (MH + 1) + 127) / 128, 128, 0, s>>>(w.H1, MH, w.D2, MH, M, gW2, gb2);
-  k_mlp_wgrad<<<(C * (MH + 1) + 127) / 128, 128, 0, s>>>(w.H2, MH, w.DY, C, M, gW3, gb3);
+  const dim3 wb(32, WG_ROWS);
+  k_mlp_wgrad<<<dim3(MH, (MIN_ + 32) / 32), wb, 0, s>>>(w.X, MIN_, w.D1, MH, M, gW1, gb1);
+  k_mlp_wgrad<<<dim3(MH, (MH + 32) / 32), wb, 0, s>>>(w.H1, MH, w.D2, MH, M, gW2, gb2);
+  k_mlp_wgrad<<<dim3(C, (MH + 32) / 32), wb, 0, s>>>(w.H2, MH, w.DY, C, M, gW3, gb3);
   k_mlp_loss<<<1, 32, 0, s>>>(w.rowloss, M, w.msum, w.losses, w.step);
   return cudaGetLastError();
 }

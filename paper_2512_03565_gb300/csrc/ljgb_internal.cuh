@@ -304,7 +304,7 @@ struct Ctx {
   double L = 0, rc = 0, skin = 0, eps = 1, sigma = 1, mass = 1;
   int prec = LJ_PREC_FP32_ACC64;
   cudaStream_t stream = nullptr;
-  int nc_lc = 0, nc_vl = 0;
+  int nc_lc = 0, nc_vl = 0, nc_lcs = 0;  // cells per axis: edge >= r_c, >= r_c + skin, >= r_c / 2
   LJParams P{};            // params with the cutoff r_c
   uint64_t Rl2 = 0;        // floor((r_l/u)^2)
   float rl2p_lo = 0, rl2p_hi = 0;  // coarse_r2 screening thresholds for r_l

@@ -47,7 +47,7 @@ lj_status time_config(lj_ctx* h, const lj_config& cfg, int samples, double& ms) 
     return tfail(c, LJ_ERR_CUDA, "cudaEventCreate");
   double total = 0.0;
   for (int s = 0; s < samples && st == LJ_OK; ++s) {
-    if (cfg.container == LJ_LC) c.moved = true;  // a step's rebin is part of the cost
+    if (cfg.container == LJ_LC || cfg.container == LJ_LCS) c.moved = true;  // a step's rebin is part of the cost
     cudaEventRecord(e0, c.stream);
     st = lj_compute_forces(h, cfg, nullptr, nullptr);
     cudaEventRecord(e1, c.stream);
@@ -57,7 +57,7 @@ lj_status time_config(lj_ctx* h, const lj_config& cfg, int samples, double& ms) 
     total += t;
   }
   double build = 0.0;
-  if (st == LJ_OK && cfg.container != LJ_LC) {
+  if (st == LJ_OK && cfg.container != LJ_LC && cfg.container != LJ_LCS) {
     c.moved_since_build = true;
     c.vl_valid = false;  // force one rebuild to time it
     c.vcl_valid = false;
@@ -137,7 +137,10 @@ lj_status lj_tune(lj_ctx* h, int32_t kind, int32_t samples, lj_config* chosen, d
   };
   // configurations usable on this machine (both cell grids need >= 3 cells per axis)
   auto usable = [&](const lj_config& g) {
-    return lj_config_valid(g) && (g.container == LJ_LC ? c.nc_lc >= 3 : g.container == LJ_VL ? c.nc_vl >= 3 : true);
+    return lj_config_valid(g) && (g.container == LJ_LC    ? c.nc_lc >= 3
+                                  : g.container == LJ_LCS ? c.nc_lcs >= 5
+                                  : g.container == LJ_VL  ? c.nc_vl >= 3
+                                                          : true);
   };
   std::vector<lj_config> cand;
   if (kind == 1 && c.mlp_C > 0) {

@@ -30,7 +30,7 @@ LJ_OK, LJ_ERR_ARG, LJ_ERR_CUDA, LJ_ERR_CAPACITY, LJ_ERR_SKIN, LJ_ERR_NONFINITE, 
 STATUS_NAMES = ["LJ_OK", "LJ_ERR_ARG", "LJ_ERR_CUDA", "LJ_ERR_CAPACITY", "LJ_ERR_SKIN",
                 "LJ_ERR_NONFINITE", "LJ_ERR_TIMEOUT", "LJ_ERR_STATE", "LJ_ERR_OOM"]
 LJ_PREC_FP64, LJ_PREC_FP32_ACC64 = 0, 1
-LJ_LC, LJ_VL, LJ_VCL = 0, 1, 2
+LJ_LC, LJ_VL, LJ_VCL, LJ_LCS = 0, 1, 2, 3
 LJ_ORD_IPT_SMEM, LJ_ORD_IPT_TMA, LJ_ORD_KI, LJ_ORD_JSPLIT, LJ_ORD_ROT32, LJ_ORD_VL_IPT, LJ_ORD_CL_TILE, \
     LJ_ORD_CL_JLANE = range(8)
 LJ_N3_OFF, LJ_N3_ATOMIC, LJ_N3_TWOPASS, LJ_N3_ATOMIC_BWD = 0, 1, 2, 3
@@ -52,7 +52,7 @@ def config(container, order, param=0, newton3=LJ_N3_OFF) -> lj_config:
 
 
 def config_name(c: lj_config) -> str:
-    cont = {LJ_LC: "LC", LJ_VL: "VL", LJ_VCL: "VCL"}.get(c.container, f"c{c.container}")
+    cont = {LJ_LC: "LC", LJ_VL: "VL", LJ_VCL: "VCL", LJ_LCS: "LCS"}.get(c.container, f"c{c.container}")
     o = ORDER_NAMES[c.order] if 0 <= c.order < len(ORDER_NAMES) else f"ord{c.order}"
     p = f"-{c.param}" if c.param else ""
     n3 = ["N3off", "N3atomic", "N3twopass", "N3bwd"][c.newton3] if 0 <= c.newton3 <= 3 else f"n3={c.newton3}"

@@ -57,7 +57,7 @@ def test_init_domain_rejects_bad_arguments_on_host(lj):
 def test_config_space(lj):
     cfgs = lj.configs()
     names = [lj.config_name(c) for c in cfgs]
-    assert len(names) == len(set(names)) == 55
+    assert len(names) == len(set(names)) == 64
     assert all(lj.load().lj_config_valid(c) for c in cfgs)
     # invalid combinations are masked (cf. the paper's lc_c01, usable only without Newton3)
     for bad in [lj.config(lj.LJ_LC, lj.LJ_ORD_VL_IPT), lj.config(lj.LJ_LC, lj.LJ_ORD_KI, 3),
@@ -67,7 +67,9 @@ def test_config_space(lj):
                 lj.config(lj.LJ_VL, lj.LJ_ORD_VL_IPT, 0, lj.LJ_N3_ATOMIC_BWD),
                 lj.config(lj.LJ_LC, lj.LJ_ORD_ROT32, 0, 4), lj.config(lj.LJ_VCL, lj.LJ_ORD_CL_TILE, 5),
                 lj.config(lj.LJ_VCL, lj.LJ_ORD_JSPLIT, 4), lj.config(lj.LJ_VCL, lj.LJ_ORD_CL_JLANE, 8, 2),
-                lj.config(lj.LJ_LC, lj.LJ_ORD_CL_TILE, 4), lj.config(3, 0)]:
+                lj.config(lj.LJ_LC, lj.LJ_ORD_CL_TILE, 4), lj.config(3, 0),
+                lj.config(lj.LJ_LCS, lj.LJ_ORD_JSPLIT, 32), lj.config(lj.LJ_LCS, lj.LJ_ORD_IPT_SMEM),
+                lj.config(lj.LJ_LCS, lj.LJ_ORD_JSPLIT, 4, lj.LJ_N3_TWOPASS), lj.config(4, 3, 4)]:
         assert not lj.load().lj_config_valid(bad)
 
 

@@ -26,7 +26,7 @@ def test_full_search_returns_argmin_of_its_evidence(lj):
     d.set_particles(s.pos, s.vel)
     cfg, times = d.tune(0, 2)
     timed = {k: v for k, v in times.items() if not np.isnan(v)}
-    assert len(timed) == 55
+    assert len(timed) == 64
     assert lj.config_name(cfg) == min(timed, key=timed.get)
     d.close()
 
@@ -37,7 +37,7 @@ def test_learned_tuner_without_model_falls_back_to_full_search(lj):
     d.set_particles(s.pos, s.vel)
     cfg, times = d.tune(1, 1)
     assert lj.load().lj_config_valid(cfg)
-    assert sum(not np.isnan(v) for v in times.values()) == 55
+    assert sum(not np.isnan(v) for v in times.values()) == 64
     d.close()
 
 
@@ -94,7 +94,7 @@ def test_energy_counter_and_energy_tuner(lj):
     cfg, ev = d.tune_energy(min_ms=5 * period)
     d.close()
     ran = {k: v for k, v in ev.items() if not np.isnan(v[1])}
-    assert len(ran) == 55
+    assert len(ran) == 64
     # power = energy / time per evaluation: a busy GB300 draws between its
     # idle floor and its 1.4 kW limit
     assert all(v[0] > 0 and 100.0 < v[1] / v[0] < 1500.0 for v in ran.values())

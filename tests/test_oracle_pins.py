@@ -566,6 +566,61 @@ def test_half_shells_cover_every_pair_once(orc, backward):
         assert set(got) == bf, name
 
 
+def _subcell_pairs(pos, L, r, half, backward=False):
+    """Pairs found by visiting, for every particle, the 5 x 5 x 5 cells of edge
+    >= r/2 around its own (the sub-cell container): all of them, or (Newton-3)
+    the half after (before) the own cell in (dz, dy, dx) offset order with j
+    after (before) i in the own cell; plain Python on the oracle's cell order."""
+    import oracle as orc
+    n = pos.shape[1]
+    nc = orc.ncells(L, 0.5 * r)
+    assert nc >= 5
+    perm, cs = orc.bin_cells(pos, nc)
+    slot = np.empty(n, dtype=np.int64)
+    slot[perm] = np.arange(n)
+    R2max = orc.cut2_int(L, r)
+    sgn = -1 if backward else 1
+    offs = [(dz, dy, dx) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)]
+    if half:
+        offs = [o for o in offs if (o[0], o[1], o[2]) > (0, 0, 0)]
+    out = []
+    for i in range(n):
+        ci = [int((int(pos[a, i]) * nc) >> 32) for a in range(3)]
+        c_lin = (ci[2] * nc + ci[1]) * nc + ci[0]
+        own = list(perm[cs[c_lin]:cs[c_lin + 1]])
+        cand = [j for j in own if sgn * (slot[j] - slot[i]) > 0] if half else [j for j in own if j != i]
+        for dz, dy, dx in offs:
+            if (dz, dy, dx) == (0, 0, 0):
+                continue
+            z, y, x = (ci[2] + sgn * dz) % nc, (ci[1] + sgn * dy) % nc, (ci[0] + sgn * dx) % nc
+            c2 = (z * nc + y) * nc + x
+            cand += list(perm[cs[c2]:cs[c2 + 1]])
+        for j in cand:
+            R2 = orc.r2_int(pos[:, i], pos[:, j])
+            if 0 < R2 <= R2max:
+                out.append((min(i, int(j)), max(i, int(j))))
+    return out
+
+
+@pytest.mark.parametrize("half,backward", [(0, False), (1, False), (1, True)])
+def test_subcell_stencil_covers_every_pair(orc, half, backward):
+    """The 5 x 5 x 5 stencil of cells of edge >= r_c / 2 finds every pair of the
+    brute force, each once from either side (full) or exactly once (either half
+    shell), on boxes of 5 to 9 cells per axis."""
+    rng = np.random.default_rng(17)
+    cases = [("uniform", 2.6, rng.integers(0, TWO32, size=(3, 60), dtype=np.uint64).astype(np.uint32)),
+             ("uniform9", 4.6, rng.integers(0, TWO32, size=(3, 150), dtype=np.uint64).astype(np.uint32)),
+             ("crowded", 3.0, rng.integers(0, 2 ** 30, size=(3, 70), dtype=np.uint64).astype(np.uint32))]
+    for name, L, pos in cases:
+        got = _subcell_pairs(pos, L, 1.0, half, backward)
+        bf = {tuple(int(v) for v in p) for p in orc.pairs_bruteforce(pos, L, 1.0)}
+        if half:
+            assert len(got) == len(set(got)), name
+            assert set(got) == bf, name
+        else:
+            assert len(got) == 2 * len(bf) and set(got) == bf, name
+
+
 # --- sampled forces (the checker of the full-size GPU runs) --------------------
 
 def _sampled_cases():
