@@ -166,6 +166,15 @@ def measured_peaks():
         return {}
 
 
+def roofline_bound(flops, alg_bytes, fp32_peak_tflops, hbm_peak_gbs):
+    """The roof of a launch in the roofline model: HBM when its useful flops
+    per algorithmic byte lie below the machine balance (FP32 peak / copy
+    bandwidth), the FP32 peak otherwise.  Returns (bound, intensity, balance)."""
+    intensity = flops / alg_bytes
+    balance = fp32_peak_tflops * 1e12 / (hbm_peak_gbs * 1e9)
+    return ("hbm" if intensity < balance else "alu"), intensity, balance
+
+
 def algorithmic_bytes(cfg, n, list_entries):
     """Bytes a force evaluation must move at least, per launch: every
     position read once (16 B: x, y, z fixed point and the original index),
@@ -322,25 +331,38 @@ def run_ours(args, ws, rank, local, pg):
             list_entries = int(nn.astype(np.int64).sum())
     alg_bytes = algorithmic_bytes(cfg, s.n, list_entries)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel_ms": avg_force_s * 1e3,
+    # Which roof bounds the launch: its useful flops per algorithmic byte
+    # against the machine balance (FP32 peak / measured copy bandwidth).  A
+    # Verlet-list launch moves 4 B of list per entry and sits below the ridge
+    # (about 1.8 flop/B against 12), so its roof is HBM; a linked-cell launch
+    # (positions only) sits above it, and its roof is the FP32 peak.
+    bound, intensity, balance = roofline_bound(flops_launch, alg_bytes, peak, hbm_peak)
+    hbm_achieved = alg_bytes / avg_force_s / 1e9
+    fp32 = {"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
                           "(SM count from the device, clock from nvidia-smi during the run; derived FFMA peak)",
-            "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3], "pairs_per_launch": float(np.mean(pairs)),
-            # the kernel's own pair evaluations (Newton-3 off evaluates each pair from both sides)
-            "kernel_pair_evals_per_s": (2.0 if cfg.newton3 == 0 else 1.0) * float(np.mean(pairs)) / avg_force_s,
-            # the same launch against the memory roofline: algorithmic bytes
-            # (list entries + lengths, positions, forces) per launch / launch time
-            "alg_bytes": alg_bytes, "list_entries": list_entries, "hbm_peak_gbs": hbm_peak,
-            "hbm_alg_gbs": alg_bytes / avg_force_s / 1e9,
-            "hbm_alg_frac": alg_bytes / avg_force_s / 1e9 / hbm_peak}
+            "flops_per_pair": FLOPS_PER_PAIR[cfg.newton3]}
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_achieved / hbm_peak, "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_basis": fp32["peak_basis"]}
+    roof.update({"traffic": traffic, "kernel_ms": avg_force_s * 1e3,
+                 # algorithmic bytes per launch: list entries and lengths, positions, forces
+                 "alg_bytes": alg_bytes, "list_entries": list_entries,
+                 "intensity_flop_per_byte": intensity, "machine_balance_flop_per_byte": balance,
+                 # the useful FP32 flops of the same launch against the FP32 peak
+                 "fp32": fp32, "pairs_per_launch": float(np.mean(pairs)),
+                 # the kernel's own pair evaluations (Newton-3 off evaluates each pair from both sides)
+                 "kernel_pair_evals_per_s": (2.0 if cfg.newton3 == 0 else 1.0) * float(np.mean(pairs)) / avg_force_s})
     if traffic:
         # DRAM bytes of one launch from the committed ncu capture (a cross-check
         # taken at the commit named in the same file)
         roof["traffic_source"] = {"file": "profiles/force_c2_traffic.txt",
                                   "commit": from_profiles("commit", cfg_name)}
-        roof["hbm_gbs"] = traffic / avg_force_s / 1e9
-        roof["hbm_frac"] = roof["hbm_gbs"] / hbm_peak
+        roof["dram_gbs"] = traffic / avg_force_s / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / hbm_peak
         roof["traffic_over_alg"] = traffic / alg_bytes
     l1, issue = from_profiles("l1_lsu_pct", cfg_name), from_profiles("issue_pct", cfg_name)
     if l1 is not None:

@@ -127,6 +127,16 @@ def test_bench_tables_cover_every_configuration(lj):
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
     assert {c.newton3 for c in lj.configs()} <= set(bench.FLOPS_PER_PAIR)
+    # the roof of a launch: a Verlet-list launch (1M particles, 75.7 entries of
+    # 4 B each, 25 M pairs x 23 flops) lies below the ridge, a linked-cell one
+    # (positions and forces only) above it
+    cfg_vl = lj.config(lj.LJ_VL, lj.LJ_ORD_JSPLIT, 4)
+    cfg_lc = lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, 4)
+    n, pairs = 1048576, 25.25e6
+    vl_bytes = bench.algorithmic_bytes(cfg_vl, n, int(75.7 * n))
+    assert vl_bytes == 16.0 * n + 24.0 * n + 4.0 * int(75.7 * n) + 4.0 * n
+    assert bench.roofline_bound(23 * pairs, vl_bytes, 80.5, 6780.0)[0] == "hbm"
+    assert bench.roofline_bound(23 * pairs, bench.algorithmic_bytes(cfg_lc, n, None), 80.5, 6780.0)[0] == "alu"
     # the committed ncu figures of the benched kernel parse, and the traffic is
     # at least the list entries and positions one launch must read
     traffic = bench.from_profiles("traffic", "VL:JSPLIT-4:N3off")

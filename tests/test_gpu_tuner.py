@@ -48,17 +48,21 @@ def test_learned_tuner_without_model_falls_back_to_full_search(lj):
 ], ids=["fluid-0.4", "slab-0.5", "fcc-1.0"])
 def test_learned_tuner_gain_on_held_out_systems(lj, system):
     """The learned choice (features -> network, no timing) is measured against
-    full search on systems absent from the training data; it must be within
-    15% of the measured best, no worse than the paper's default order (1/V, here
-    VL:JSPLIT-32), and cost a small fraction of full search's tuning time."""
+    full search on systems absent from the training data; it must be within 5%
+    of the measured best (the tuner target; each configuration's time is the
+    median of three full searches of 3 evaluations each), no worse than the
+    paper's default order (1/V, here VL:JSPLIT-32), and cost a small fraction
+    of one full search's tuning time."""
     from paper_2512_03565_gb300 import tuner
     s = system()
     model = tuner.load()
     d = lj.Domain(s.L, s.rc, s.skin)
     d.set_particles(s.pos, s.vel)
     t0 = time.perf_counter()
-    _, times = d.tune(0, 3)
+    runs = [d.tune(0, 3)[1]]
     t_full = time.perf_counter() - t0
+    runs += [d.tune(0, 3)[1] for _ in range(2)]
+    times = {k: float(np.median([r[k] for r in runs])) for k in runs[0]}
     tuner.install(d, model)
     t0 = time.perf_counter()
     learned, _ = d.tune(1, 0)
@@ -67,7 +71,7 @@ def test_learned_tuner_gain_on_held_out_systems(lj, system):
     best = min(v for v in times.values() if not np.isnan(v))
     t_l = times[lj.config_name(learned)]
     t_default = times["VL:JSPLIT-32:N3off"]
-    assert t_l <= 1.15 * best, (lj.config_name(learned), t_l, best)
+    assert t_l <= 1.05 * best, (lj.config_name(learned), t_l, best)
     assert t_l <= t_default * 1.02
     assert t_learned < 0.1 * t_full
 
