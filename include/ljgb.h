@@ -316,6 +316,19 @@ lj_status lj_mlp_loss_grad(const float* params, int32_t C, const float* X, const
 lj_status lj_mlp_train(const float* X, const float* T, const float* mask, int64_t M, int32_t C, float* params,
                        int32_t epochs, float lr, float* losses, void* stream);
 
+/* The training inputs of the learned tuner, computed on the GPU from the
+ * full-search timings and the features (data-driven tuning, Sec. 6; no
+ * counterpart code in the paper).  T: M x C timings (host, row-major,
+ * double; NaN or a non-positive value = not timed); X: M x 16 features
+ * (host, double).  Outputs (host, float): Y[M][C] = log(t / t_best) of each
+ * row's valid entries (0 elsewhere), mask[M][C] = 1 where valid, and the
+ * standardised features Xs[M][16] = (X - mean) / std with the columns' mean[16]
+ * and population standard deviation std[16] (a deviation below 1e-12 becomes
+ * 1).  Synchronises stream (a cudaStream_t or NULL).  Errors: LJ_ERR_ARG,
+ * LJ_ERR_OOM, LJ_ERR_CUDA. */
+lj_status lj_tuner_prepare(const double* T, int64_t M, int32_t C, const double* X, float* Y, float* mask, float* Xs,
+                           float* mean, float* std, void* stream);
+
 /* Copy out forces (3*n doubles, original order).  Synchronises if on_device = 0. */
 lj_status lj_get_forces(lj_ctx* ctx, double* dst, int32_t on_device);
 

@@ -92,6 +92,8 @@ def _load():
             "orc_mlp_forward": (None, [_F64P, i32, i64, _F64P, _F64P]),
             "orc_mlp_loss_grad": (f64, [_F64P, i32, i64, _F64P, _F64P, _F64P, _F64P]),
             "orc_adam_step": (None, [i64, _F64P, _F64P, _F64P, _F64P, f64, f64, f64, f64, i32]),
+            "orc_tuner_targets": (None, [i64, i32, _F64P, _F64P, _F64P]),
+            "orc_standardize": (None, [i64, i32, _F64P, _F64P, _F64P, _F64P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -317,3 +319,23 @@ def adam_step(params, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
     """In-place Adam step on float64 arrays params, m, v."""
     _load().orc_adam_step(params.shape[0], params, np.ascontiguousarray(grad, dtype=np.float64),
                           m, v, lr, beta1, beta2, eps, int(t))
+
+
+def tuner_targets(T):
+    """Relative log times log(t / t_best) per row and the validity mask (NaN or
+    non-positive times are not valid)."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    M, Cn = T.shape
+    Y, mask = np.zeros_like(T), np.zeros_like(T)
+    _load().orc_tuner_targets(M, Cn, T, Y, mask)
+    return Y, mask
+
+
+def standardize(X):
+    """Per-column mean and population standard deviation (below 1e-12: 1) and
+    the standardised rows.  Returns (Xs, mean, std)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    M, F = X.shape
+    Xs, mean, sd = np.zeros_like(X), np.zeros(F), np.zeros(F)
+    _load().orc_standardize(M, F, X, Xs, mean, sd)
+    return Xs, mean, sd

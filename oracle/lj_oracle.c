@@ -735,3 +735,41 @@ void orc_adam_step(int64_t P, double* p, const double* g, double* m, double* v, 
     p[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
   }
 }
+
+/* Training targets of the learned tuner (data-driven tuning, Sec. 6): per row
+ * m of timings T[M][C] (a configuration not timed is NaN, or not positive),
+ * the relative log time Y = log(T / t_best) with t_best the row's smallest
+ * valid time, and mask = 1 where valid (Y = 0, mask = 0 elsewhere). */
+void orc_tuner_targets(int64_t M, int C, const double* T, double* Y, double* mask) {
+  for (int64_t m = 0; m < M; ++m) {
+    double best = INFINITY;
+    for (int c = 0; c < C; ++c) {
+      const double t = T[m * C + c];
+      if (isfinite(t) && t > 0.0 && t < best) best = t;
+    }
+    for (int c = 0; c < C; ++c) {
+      const double t = T[m * C + c];
+      const int ok = isfinite(t) && t > 0.0;
+      Y[m * C + c] = ok ? log(t / best) : 0.0;
+      mask[m * C + c] = ok ? 1.0 : 0.0;
+    }
+  }
+}
+
+/* Feature standardisation of the tuner: mean and (population) standard
+ * deviation of each of the F columns of X[M][F] over the rows, a deviation
+ * below 1e-12 replaced by 1, and Xs = (X - mean) / std. */
+void orc_standardize(int64_t M, int F, const double* X, double* Xs, double* mean, double* sd) {
+  for (int f = 0; f < F; ++f) {
+    double s = 0.0;
+    for (int64_t m = 0; m < M; ++m) s += X[m * F + f];
+    const double mu = s / (double)M;
+    double q = 0.0;
+    for (int64_t m = 0; m < M; ++m) q += (X[m * F + f] - mu) * (X[m * F + f] - mu);
+    double sig = sqrt(q / (double)M);
+    if (sig < 1e-12) sig = 1.0;
+    mean[f] = mu;
+    sd[f] = sig;
+    for (int64_t m = 0; m < M; ++m) Xs[m * F + f] = (X[m * F + f] - mu) / sig;
+  }
+}

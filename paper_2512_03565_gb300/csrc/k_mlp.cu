@@ -174,6 +174,67 @@ __global__ void k_adam(int64_t P, float* __restrict__ p, const float* __restrict
   p[k] -= lr * (mk / corr[0]) / (sqrtf(vk / corr[1]) + eps);
 }
 
+// Training inputs of the learned tuner.  Row m of the timings (NaN or non-
+// positive = not timed): Y = log(t / t_best) over the valid entries, 0 and a
+// zero mask elsewhere; one thread per row.
+__global__ void k_tuner_targets(const double* __restrict__ T, int64_t M, int C, float* __restrict__ Y,
+                                float* __restrict__ mask) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double best = INFINITY;
+  for (int c = 0; c < C; ++c) {
+    const double t = T[m * C + c];
+    if (isfinite(t) && t > 0.0 && t < best) best = t;
+  }
+  for (int c = 0; c < C; ++c) {
+    const double t = T[m * C + c];
+    const bool ok = isfinite(t) && t > 0.0;
+    Y[m * C + c] = ok ? (float)log(t / best) : 0.0f;
+    mask[m * C + c] = ok ? 1.0f : 0.0f;
+  }
+}
+
+// Mean and population standard deviation of feature f over the rows (block
+// f; FP64 partial sums in a fixed tree order), a deviation below 1e-12
+// replaced by 1; then the standardised features.
+constexpr int STD_T = 256;
+__global__ void __launch_bounds__(STD_T) k_feature_moments(const double* __restrict__ X, int64_t M, int F,
+                                                           double* __restrict__ mom) {
+  __shared__ double sh[STD_T];
+  const int f = blockIdx.x, t = threadIdx.x;
+  double s = 0.0;
+  for (int64_t m = t; m < M; m += STD_T) s += X[m * F + f];
+  sh[t] = s;
+  __syncthreads();
+  for (int o = STD_T / 2; o > 0; o >>= 1) {
+    if (t < o) sh[t] += sh[t + o];
+    __syncthreads();
+  }
+  const double mu = sh[0] / (double)M;
+  __syncthreads();
+  double q = 0.0;
+  for (int64_t m = t; m < M; m += STD_T) q += (X[m * F + f] - mu) * (X[m * F + f] - mu);
+  sh[t] = q;
+  __syncthreads();
+  for (int o = STD_T / 2; o > 0; o >>= 1) {
+    if (t < o) sh[t] += sh[t + o];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double sd = sqrt(sh[0] / (double)M);
+    mom[2 * f] = mu;
+    mom[2 * f + 1] = sd < 1e-12 ? 1.0 : sd;
+  }
+}
+
+__global__ void k_standardize(const double* __restrict__ X, int64_t M, int F, const double* __restrict__ mom,
+                              float* __restrict__ Xs) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * F) return;
+  const int f = (int)(e % F);
+  Xs[e] = (float)((X[e] - mom[2 * f]) / mom[2 * f + 1]);
+}
+
 // Device workspace for one (M, C) problem.
 struct MlpWork {
   int64_t M = 0;
@@ -300,6 +361,45 @@ lj_status lj_mlp_loss_grad(const float* params, int32_t C, const float* X, const
   if (cudaStreamSynchronize(s) != cudaSuccess) return LJ_ERR_CUDA;
   if (loss) *loss = l;
   return LJ_OK;
+}
+
+lj_status lj_tuner_prepare(const double* T, int64_t M, int32_t C, const double* X, float* Y, float* mask, float* Xs,
+                           float* mean, float* sd, void* stream) {
+  if (!T || !X || !Y || !mask || !Xs || !mean || !sd || C < 1 || M < 1) return LJ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  double *dT = nullptr, *dX = nullptr, *dmom = nullptr;
+  float *dY = nullptr, *dM = nullptr, *dXs = nullptr;
+  const size_t nT = (size_t)M * C, nX = (size_t)M * MIN_;
+  lj_status st = LJ_OK;
+  if (cudaMalloc(&dT, nT * sizeof(double)) != cudaSuccess || cudaMalloc(&dX, nX * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dmom, 2 * MIN_ * sizeof(double)) != cudaSuccess || cudaMalloc(&dY, nT * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&dM, nT * sizeof(float)) != cudaSuccess || cudaMalloc(&dXs, nX * sizeof(float)) != cudaSuccess)
+    st = LJ_ERR_OOM;
+  std::vector<double> mom(2 * MIN_);
+  if (st == LJ_OK) {
+    cudaError_t e = cudaMemcpyAsync(dT, T, nT * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dX, X, nX * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      k_tuner_targets<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(dT, M, C, dY, dM);
+      k_feature_moments<<<MIN_, STD_T, 0, s>>>(dX, M, MIN_, dmom);
+      k_standardize<<<(unsigned)(((int64_t)nX + 255) / 256), 256, 0, s>>>(dX, M, MIN_, dmom, dXs);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Y, dY, nT * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mask, dM, nT * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Xs, dXs, nX * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mom.data(), dmom, 2 * MIN_ * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = LJ_ERR_CUDA;
+  }
+  if (st == LJ_OK)
+    for (int f = 0; f < MIN_; ++f) {
+      mean[f] = (float)mom[2 * f];
+      sd[f] = (float)mom[2 * f + 1];
+    }
+  for (void* p : {(void*)dT, (void*)dX, (void*)dmom, (void*)dY, (void*)dM, (void*)dXs})
+    if (p) cudaFree(p);
+  return st;
 }
 
 lj_status lj_mlp_train(const float* X, const float* T, const float* mask, int64_t M, int32_t C, float* params,

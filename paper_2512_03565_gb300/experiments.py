@@ -90,8 +90,7 @@ def regret_of(pred, t_row, mask_row):
 
 
 def leave_one_out(X, T, box_ids, names, epochs=2000, lr=3e-3, default="VL:JSPLIT-32:N3off", log=print):
-    _, M = tuner.targets(T)
-    M = M.astype(bool)
+    M = tuner.valid(T)
     res = []
     d_idx = names.index(default) if default in names else None
     for b in np.unique(box_ids):

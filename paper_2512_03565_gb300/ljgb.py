@@ -81,6 +81,7 @@ _SIGS = {
     "lj_get_clusters": (C.c_int, [_VP, C.POINTER(C.c_int64), _VP, C.POINTER(C.c_int32)]),
     "lj_get_cluster_lists": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int32)]),
     "lj_get_cluster_masks": (C.c_int, [_VP, _VP]),
+    "lj_tuner_prepare": (C.c_int, [_VP, C.c_int64, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "lj_compute_forces": (C.c_int, [_VP, lj_config, _VP, _VP]),
     "lj_config_valid": (C.c_int32, [lj_config]),
     "lj_config_list": (C.c_int32, [_VP, C.c_int32]),
@@ -489,6 +490,21 @@ def tune_select(timings, valid=None, reduce=0) -> int:
 
 def mlp_nparams(C_out: int) -> int:
     return 64 * 16 + 64 + 64 * 64 + 64 + C_out * 64 + C_out
+
+
+def tuner_prepare(T, X):
+    """lj_tuner_prepare: (Y, mask, Xs, mean, std), float32."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    M, Cn = T.shape
+    Y, mask = np.zeros((M, Cn), dtype=np.float32), np.zeros((M, Cn), dtype=np.float32)
+    Xs = np.zeros((M, X.shape[1]), dtype=np.float32)
+    mean, std = np.zeros(X.shape[1], dtype=np.float32), np.zeros(X.shape[1], dtype=np.float32)
+    st = load().lj_tuner_prepare(T.ctypes.data, M, Cn, X.ctypes.data, Y.ctypes.data, mask.ctypes.data,
+                                 Xs.ctypes.data, mean.ctypes.data, std.ctypes.data, None)
+    if st != LJ_OK:
+        raise LJError(st, "lj_tuner_prepare failed")
+    return Y, mask, Xs, mean, std
 
 
 def mlp_forward(params, C_out, X):

@@ -10,8 +10,9 @@ inference runs inside lj_tune kind 1.
 Targets are per-row relative log times, log(t_config / t_best), so the network
 ranks configurations; missing or invalid configurations are masked out of the
 loss.  The network's outputs are the configurations that come within 25 % of
-the best in at least one training row.  Features are standardised with the training set's mean and standard
-deviation (stored with the model).
+the best in at least one training row.  Features are standardised with the
+training set's mean and standard deviation (stored with the model).  Targets,
+masks and standardisation are computed by the library (lj_tuner_prepare).
 """
 from __future__ import annotations
 
@@ -58,12 +59,9 @@ def collect(systems, samples=3, snapshots=(0,), dt=0.002, cfg_run=None, log=None
     return np.array(X), np.array(T, dtype=np.float64), names, labels
 
 
-def targets(T):
-    """Relative log times and the validity mask."""
-    mask = np.isfinite(T) & (T > 0)
-    best = np.nanmin(np.where(mask, T, np.nan), axis=1, keepdims=True)
-    Y = np.where(mask, np.log(np.where(mask, T, 1.0) / best), 0.0)
-    return Y, mask.astype(np.float64)
+def valid(T):
+    """Timed entries of a timing table (NaN or non-positive = not timed)."""
+    return np.isfinite(T) & (T > 0)
 
 
 def candidates(T, near=1.25):
@@ -71,8 +69,16 @@ def candidates(T, near=1.25):
     only ones the network ranks (it has no evidence that the others ever win,
     and each extra output is one more chance of a wrong pick on a system
     unlike the training data)."""
-    Y, M = targets(T)
-    return (np.where(M > 0, Y, np.inf) <= math.log(near)).any(axis=0)
+    ok = valid(T)
+    best = np.min(np.where(ok, T, np.inf), axis=1, keepdims=True)
+    return (ok & (T <= near * best)).any(axis=0)
+
+
+def prepare(X, T):
+    """Training inputs on the GPU (lj_tuner_prepare): relative log times
+    log(t / t_best) per row and their mask, and the standardised features with
+    the columns' mean and standard deviation."""
+    return lj.tuner_prepare(T, X)
 
 
 def train(X, T, epochs=3000, lr=3e-3, seed=0, near=1.25):
@@ -80,13 +86,8 @@ def train(X, T, epochs=3000, lr=3e-3, seed=0, near=1.25):
     (see `candidates`).  Returns the model dict; model["keep"] marks T's
     columns that are the network's outputs, in order."""
     keep = candidates(T, near)
-    T = T[:, keep]
-    Y, M = targets(T)
-    mean = X.mean(axis=0)
-    std = X.std(axis=0)
-    std[std < 1e-12] = 1.0
-    Xs = (X - mean) / std
-    Cn = T.shape[1]
+    Y, M, Xs, mean, std = prepare(X, T[:, keep])
+    Cn = int(keep.sum())
     rng = np.random.default_rng(seed)
     P = lj.mlp_nparams(Cn)
     p0 = np.zeros(P)
@@ -98,8 +99,7 @@ def train(X, T, epochs=3000, lr=3e-3, seed=0, near=1.25):
             p0[off:off + k] = rng.normal(0.0, 1.0 / math.sqrt(sh[1]), size=k)
         off += k
     params, losses = lj.mlp_train(p0, Cn, Xs, Y, M, epochs, lr)
-    return {"params": params.astype(np.float32), "mean": mean.astype(np.float32),
-            "std": std.astype(np.float32), "C": Cn, "losses": losses, "keep": keep}
+    return {"params": params.astype(np.float32), "mean": mean, "std": std, "C": Cn, "losses": losses, "keep": keep}
 
 
 def predict(model, X):

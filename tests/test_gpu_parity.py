@@ -389,6 +389,30 @@ def test_mlp_training_reduces_loss(lj):
     assert np.abs(p3 - q).max() <= 1e-4
 
 
+def test_tuner_prepare_matches_oracle(lj):
+    """Relative log times, masks and standardised features of the learned
+    tuner's training set, GPU kernels against the oracle: timings with untimed
+    (NaN), zero and negative entries, a row with nothing timed, a constant
+    feature column; 1000 rows span several blocks with a ragged tail."""
+    rng = np.random.default_rng(12)
+    Mr, Cn = 1000, 37
+    T = np.exp(rng.normal(-1.0, 0.6, size=(Mr, Cn)))
+    T[rng.random((Mr, Cn)) < 0.1] = np.nan
+    T[3, 5], T[4, 6], T[7, :] = 0.0, -2.0, np.nan
+    X = rng.normal(2.0, 3.0, size=(Mr, 16)) * np.logspace(-3, 3, 16)
+    X[:, 9] = 0.625
+    Y, Mk, Xs, mean, sd = lj.tuner_prepare(T, X)
+    Yr, Mr_ = oracle.tuner_targets(T)
+    Xr, mr, sr = oracle.standardize(X)
+    np.testing.assert_array_equal(Mk, Mr_)
+    np.testing.assert_array_equal(Mk[7], 0.0)
+    np.testing.assert_allclose(Y, Yr, rtol=2e-7, atol=1e-7)       # FP64 arithmetic, FP32 output
+    np.testing.assert_allclose(mean, mr, rtol=2e-7, atol=1e-30)
+    np.testing.assert_allclose(sd, sr, rtol=2e-7)
+    assert sd[9] == 1.0 and np.all(Xs[:, 9] == 0.0)
+    np.testing.assert_allclose(Xs, Xr, rtol=2e-7, atol=1e-6)
+
+
 def test_capacity_regrowth_and_skin_rebuild(lj):
     s = W.fcc(4000, 1.2, 5)                       # dense: lists longer than the initial estimate
     d = lj.Domain(s.L, s.rc, 0.6)

@@ -12,12 +12,36 @@ import oracle
 from paper_2512_03565_gb300 import tuner
 
 
-def test_targets_are_relative_log_times():
-    T = np.array([[2.0, 1.0, np.nan, 4.0], [3.0, 3.0, 6.0, 1.5]])
-    Y, M = tuner.targets(T)
-    np.testing.assert_allclose(Y[0], [np.log(2.0), 0.0, 0.0, np.log(4.0)])
-    np.testing.assert_allclose(Y[1], [np.log(2.0), np.log(2.0), np.log(4.0), 0.0])
-    np.testing.assert_array_equal(M, [[1, 1, 0, 1], [1, 1, 1, 1]])
+def test_oracle_targets_are_relative_log_times():
+    """Hand-built rows: the best entry is 0, the others log of their ratio to
+    it; untimed (NaN), zero and negative entries are masked; a row with no
+    valid entry is all masked; scaling a row leaves its targets unchanged."""
+    oracle.build()
+    T = np.array([[2.0, 1.0, np.nan, 4.0], [3.0, 3.0, 6.0, 1.5], [np.nan, 0.0, -1.0, np.inf]])
+    Y, M = oracle.tuner_targets(T)
+    np.testing.assert_allclose(Y[0], [np.log(2.0), 0.0, 0.0, np.log(4.0)], rtol=1e-15)
+    np.testing.assert_allclose(Y[1], [np.log(2.0), np.log(2.0), np.log(4.0), 0.0], rtol=1e-15)
+    np.testing.assert_array_equal(M, [[1, 1, 0, 1], [1, 1, 1, 1], [0, 0, 0, 0]])
+    np.testing.assert_array_equal(Y[2], 0.0)
+    Y2, M2 = oracle.tuner_targets(T * 7.25)
+    np.testing.assert_allclose(Y2[:2], Y[:2], atol=1e-15)
+    np.testing.assert_array_equal(M2, M)
+
+
+def test_oracle_standardization_is_numpy_mean_and_std():
+    """Against numpy's mean and population std (a textbook routine); a
+    constant column keeps std 1 and standardises to 0."""
+    oracle.build()
+    rng = np.random.default_rng(4)
+    X = rng.normal(3.0, 2.0, size=(200, 16))
+    X[:, 5] = 4.0
+    Xs, mean, sd = oracle.standardize(X)
+    np.testing.assert_allclose(mean, X.mean(axis=0), rtol=1e-13)
+    want = X.std(axis=0)
+    want[5] = 1.0
+    np.testing.assert_allclose(sd, want, rtol=1e-12)
+    np.testing.assert_allclose(Xs, (X - mean) / sd, rtol=1e-13, atol=1e-14)
+    np.testing.assert_array_equal(Xs[:, 5], 0.0)
 
 
 def test_candidates_are_the_configurations_near_some_best():
@@ -43,7 +67,7 @@ def test_committed_model_ranks_its_training_rows():
     cols = np.array([names.index(n) for n in out_names])
     oracle.build()
     Y = oracle.mlp_forward(params, C, (X - mean) / std)
-    _, M = tuner.targets(T)
+    M = tuner.valid(T)
     regrets = []
     for r in range(X.shape[0]):
         p = np.where(M[r, cols] > 0, Y[r], np.inf)
