@@ -1,6 +1,7 @@
 """Run-time tuning on the GPU: full search (Sec. 2.3.2) and the learned tuner
 (Sec. 6's data-driven tuning) with the committed model trained on GB300
 timings of the density sweep."""
+import os
 import time
 
 import numpy as np
@@ -46,6 +47,8 @@ def test_learned_tuner_without_model_falls_back_to_full_search(lj):
     lambda: W.slab(400000, 0.8, 0.02, 0.5, 998),
     lambda: W.fcc(250000, 1.0, 997),
 ], ids=["fluid-0.4", "slab-0.5", "fcc-1.0"])
+@pytest.mark.skipif(os.environ.get("LJGB_CHECKS", "0") not in ("", "0"),
+                    reason="the network ranks the production kernels; the index-check build shifts their relative cost")
 def test_learned_tuner_gain_on_held_out_systems(lj, system):
     """The learned choice (features -> network, no timing) is measured against
     full search on systems absent from the training data; it must be within 5%
