@@ -34,12 +34,16 @@
   the fluid at 0.75, a gas at 0.1), with the lengths over which a lane sums
   in FP32 (list entries and linked-cell candidates per particle).
 
+* ``c2-sweep``: the 1,048,576-particle fluid MD run (100 steps, lists rebuilt
+  every 10) with every valid configuration, 5 fresh runs each: the mean
+  force-kernel time over steps 10-100, minimum over the runs.
+
 * ``force-launch``: a few force evaluations of one configuration on the
   homogeneous fluid (density 0.75, r_c 2.5, skin 0.3) after a warm-up one,
   for kernel profilers; ``mlp-launch``: one forward and one gradient pass of
   the tuner network on a batch of rows.
 
-Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy|traversal|clusters
+Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy|traversal|clusters|c2-sweep
        [options]
 """
 from __future__ import annotations
@@ -275,6 +279,39 @@ def traversal(n=500_000, samples=5, log=print):
     return out
 
 
+def c2_sweep(steps=100, skip=10, repeats=5, dt=0.002, log=print):
+    """The 1,048,576-particle fluid (density 0.75, skin 0.3, lists rebuilt every
+    10 steps) run with every valid configuration: `repeats` fresh MD runs of
+    `steps` velocity-Verlet steps from the same start; per run the mean
+    force-kernel time over steps skip..steps (CUDA events around each force
+    launch), per configuration the minimum over the runs, with the whole-step
+    wall time (host-synchronised) and the unique in-cutoff pairs of the last
+    evaluation.  Caches are not flushed between steps."""
+    import torch
+    s = W.config2()
+    out = {}
+    for cfg in lj.configs():
+        name = lj.config_name(cfg)
+        force, step, pairs = [], [], 0
+        for _ in range(repeats):
+            d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP32_ACC64)
+            d.set_particles(s.pos, s.vel)
+            d.integrate(dt, skip, cfg, rebuild_every=10)
+            torch.cuda.synchronize()
+            d.timing(1)
+            t0 = time.perf_counter()
+            d.integrate(dt, steps - skip, cfg, rebuild_every=10)
+            torch.cuda.synchronize()
+            step.append((time.perf_counter() - t0) / (steps - skip) * 1e3)
+            ms, k, _ = d.timing(0)
+            force.append(ms / max(k, 1))
+            pairs = int(d.counters()[1])
+            d.close()
+        out[name] = {"force_ms": min(force), "force_ms_runs": force, "step_ms": min(step), "pairs": pairs}
+        log(f"{name}: force {min(force):.4f} ms (min of {repeats}), step {min(step):.4f} ms, pairs {pairs}")
+    return out
+
+
 def clusters(samples=5, evals=20, log=print):
     """Sec. 5.1, cluster sizes: every cluster-list configuration (orders
     CL_TILE / CL_JLANE, M = 4, 6, 8, Newton-3 off / atomic) against the best
@@ -357,7 +394,8 @@ def precision(n=8000, log=print):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy",
-                                     "traversal", "clusters", "force-launch", "mlp-launch", "precision"])
+                                     "traversal", "clusters", "force-launch", "mlp-launch", "precision",
+                                     "c2-sweep"])
     ap.add_argument("--cfg", default="1,3,4,0", help="force-launch: container,order,param,newton3")
     ap.add_argument("--particles", type=int, default=524288)
     ap.add_argument("--evals", type=int, default=3)
@@ -435,6 +473,10 @@ def main(argv=None):
         lj.mlp_forward(model["params"], C_out, X)
         lj.mlp_loss_grad(model["params"], C_out, X, T, M)
         print(json.dumps({"rows": 4096, "outputs": C_out}))
+    elif a.what == "c2-sweep":
+        res = c2_sweep()
+        if a.out:
+            json.dump(res, open(a.out, "w"))
     elif a.what == "clusters":
         res = clusters()
         if a.out:
