@@ -9,7 +9,7 @@ inference runs inside lj_tune kind 1.
 
 Targets are per-row relative log times, log(t_config / t_best), so the network
 ranks configurations; missing or invalid configurations are masked out of the
-loss.  The network's outputs are the configurations that come within 25 % of
+loss.  The network's outputs are the configurations that come within 10 % of
 the best in at least one training row.  Features are standardised with the
 training set's mean and standard deviation (stored with the model).  Targets,
 masks and standardisation are computed by the library (lj_tuner_prepare).
@@ -64,7 +64,7 @@ def valid(T):
     return np.isfinite(T) & (T > 0)
 
 
-def candidates(T, near=1.25):
+def candidates(T, near=1.10):
     """Configurations within `near` of some row's best in the timings T: the
     only ones the network ranks (it has no evidence that the others ever win,
     and each extra output is one more chance of a wrong pick on a system
@@ -81,7 +81,7 @@ def prepare(X, T):
     return lj.tuner_prepare(T, X)
 
 
-def train(X, T, epochs=3000, lr=3e-3, seed=0, near=1.25):
+def train(X, T, epochs=3000, lr=3e-3, seed=0, near=1.10):
     """Trains the network on the GPU over the candidate configurations of T
     (see `candidates`).  Returns the model dict; model["keep"] marks T's
     columns that are the network's outputs, in order."""

@@ -4,7 +4,7 @@ The network is evaluated with the FP64 oracle's forward pass (independent of
 the GPU kernels that trained it): it must rank the configurations of its own
 training rows (GB300 full-search timings of the density sweep) close to the
 measured best over all timed configurations, of which it ranks the candidates
-(those within 25 % of some row's best)."""
+(those within 10 % of some row's best)."""
 import numpy as np
 import pytest
 
@@ -45,10 +45,10 @@ def test_oracle_standardization_is_numpy_mean_and_std():
 
 
 def test_candidates_are_the_configurations_near_some_best():
-    # config 0 best in row 0; config 1 within 25 % in row 1; config 2 never within 25 %;
+    # config 0 best in row 0; config 1 within 25 % (not 10 %) in row 1; config 2 never within 25 %;
     # config 3 best in row 1 but missing (NaN) in row 0
     T = np.array([[1.0, 1.5, 2.0, np.nan], [2.0, 1.2, 3.0, 1.0]])
-    np.testing.assert_array_equal(tuner.candidates(T), [True, True, False, True])
+    np.testing.assert_array_equal(tuner.candidates(T, near=1.25), [True, True, False, True])
     np.testing.assert_array_equal(tuner.candidates(T, near=1.1), [True, False, False, True])
 
 
