@@ -41,7 +41,10 @@
 * ``force-launch``: a few force evaluations of one configuration on the
   homogeneous fluid (density 0.75, r_c 2.5, skin 0.3) after a warm-up one,
   for kernel profilers; ``mlp-launch``: one forward and one gradient pass of
-  the tuner network on a batch of rows.
+  the tuner network on a batch of rows; ``aux-launch``: the auxiliary kernels
+  (features, pair lister, 16-bit list copy, getters, quantisation, the
+  allocation-free binning, tuner training inputs, a few training epochs) once
+  each on a 60,000-particle fluid.
 
 Usage: python -m paper_2512_03565_gb300.experiments sweep|train|droplet|ensemble|ensemble-launch|energy|traversal|clusters|c2-sweep
        [options]
@@ -395,7 +398,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["sweep", "train", "droplet", "ensemble", "ensemble-launch", "energy",
                                      "traversal", "clusters", "force-launch", "mlp-launch", "precision",
-                                     "c2-sweep"])
+                                     "c2-sweep", "aux-launch"])
     ap.add_argument("--cfg", default="1,3,4,0", help="force-launch: container,order,param,newton3")
     ap.add_argument("--particles", type=int, default=524288)
     ap.add_argument("--evals", type=int, default=3)
@@ -463,6 +466,44 @@ def main(argv=None):
         print(json.dumps({"config": lj.config_name(cfg), "n": s.n, "evals": a.evals,
                           "force_kernel_ms": ms / max(k, 1)}))
         d.close()
+    elif a.what == "aux-launch":
+        # the library's auxiliary kernels, each launched at least once on a
+        # 60,000-particle fluid (small enough for the 16-bit list copy)
+        s = W.stratified(60000, 0.75, W.BASE_SEED + 91)
+        d = lj.Domain(s.L, s.rc, s.skin)
+        d.set_particles(s.pos, s.vel)
+        d.features()
+        d.pairs(lj.LJ_LC)
+        cfg = lj.config(lj.LJ_VL, lj.LJ_ORD_JSPLIT, 4, lj.LJ_N3_OFF)
+        d.compute_forces(cfg)
+        d.verlet()
+        d.integrate(0.002, 2, cfg)
+        d.state()
+        d.kinetic_energy()
+        d.forces()
+        d.close()
+        d = lj.Domain(s.L, s.rc, s.skin)                       # coordinates as doubles: quantised on the GPU
+        d.set_particles(np.ascontiguousarray((s.pos.astype(np.float64) + 0.5) * (s.L / 2.0 ** 32)), s.vel)
+        d.compute_forces(lj.config(lj.LJ_LC, lj.LJ_ORD_JSPLIT, 2, lj.LJ_N3_OFF))
+        d.close()
+        import torch                                           # the allocation-free binning entry point
+        dev = torch.device("cuda", 0)
+        nc = int(np.floor(s.L / s.rc))
+        pos_d = torch.from_numpy(s.pos.view(np.int32)).to(dev).contiguous()
+        perm_d = torch.zeros(s.n, dtype=torch.int32, device=dev)
+        cs_d = torch.zeros(nc ** 3 + 1, dtype=torch.int32, device=dev)
+        st = lj.load().lj_bin_cells_static(pos_d.data_ptr(), s.n, nc, perm_d.data_ptr(), cs_d.data_ptr(),
+                                           torch.cuda.current_stream(dev).cuda_stream)
+        if st != lj.LJ_OK:
+            raise lj.LJError(st, "lj_bin_cells_static failed")
+        torch.cuda.synchronize(dev)
+        rng = np.random.default_rng(6)
+        T = np.exp(rng.normal(size=(174, 64)))
+        X = rng.normal(size=(174, 16))
+        Y, M, Xs, _, _ = lj.tuner_prepare(T, X)
+        p0 = rng.normal(0, 0.1, size=lj.mlp_nparams(64))
+        lj.mlp_train(p0, 64, Xs, Y, M, 3, 3e-3)
+        print(json.dumps({"n": s.n, "rows": 174}))
     elif a.what == "mlp-launch":
         model = tuner.load()
         rng = np.random.default_rng(5)
