@@ -176,17 +176,21 @@ __global__ void k_adam(int64_t P, float* __restrict__ p, const float* __restrict
 
 // Training inputs of the learned tuner.  Row m of the timings (NaN or non-
 // positive = not timed): Y = log(t / t_best) over the valid entries, 0 and a
-// zero mask elsewhere; one thread per row.
+// zero mask elsewhere; one warp per row, its lanes over the configurations
+// (the row's best by a warp minimum).
 __global__ void k_tuner_targets(const double* __restrict__ T, int64_t M, int C, float* __restrict__ Y,
                                 float* __restrict__ mask) {
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
+  const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (m >= M) return;  // whole warps leave together
   double best = INFINITY;
-  for (int c = 0; c < C; ++c) {
+  for (int c = lane; c < C; c += 32) {
     const double t = T[m * C + c];
     if (isfinite(t) && t > 0.0 && t < best) best = t;
   }
-  for (int c = 0; c < C; ++c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  for (int c = lane; c < C; c += 32) {
     const double t = T[m * C + c];
     const bool ok = isfinite(t) && t > 0.0;
     Y[m * C + c] = ok ? (float)log(t / best) : 0.0f;
@@ -380,7 +384,7 @@ lj_status lj_tuner_prepare(const double* T, int64_t M, int32_t C, const double* 
     cudaError_t e = cudaMemcpyAsync(dT, T, nT * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dX, X, nX * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-      k_tuner_targets<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(dT, M, C, dY, dM);
+      k_tuner_targets<<<(unsigned)((M + 3) / 4), 128, 0, s>>>(dT, M, C, dY, dM);
       k_feature_moments<<<MIN_, STD_T, 0, s>>>(dX, M, MIN_, dmom);
       k_standardize<<<(unsigned)(((int64_t)nX + 255) / 256), 256, 0, s>>>(dX, M, MIN_, dmom, dXs);
       e = cudaGetLastError();
