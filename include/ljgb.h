@@ -6,14 +6,17 @@
  *   - the pairwise force sum F_i = sum_j F_ij (Sec. 2.1, Eq. 1) over pairs
  *     within the cutoff (Sec. 2.1), Lennard-Jones 12-6 (named in Sec. 4.1;
  *     textbook form U = 4 eps [(sigma/r)^12 - (sigma/r)^6], truncated);
- *   - neighbour identification by Linked Cells and by Verlet lists with a skin
- *     (Sec. 2.1.1);
+ *   - neighbour identification by Linked Cells (cells of edge >= r_c, or
+ *     sub-cells of edge >= r_c/2), by Verlet lists with a skin and by Verlet
+ *     cluster lists (Sec. 2.1.1);
  *   - the interaction order, i.e. which particles of the two lists a functor
  *     holds against which (Sec. 4.1, Fig. 4: 1/V, V/1, 2/V2, V2/2), as GPU
  *     orders chosen at run time; Newton's third law on or off (Sec. 4.1.3);
  *   - the full-search auto-tuner over the Cartesian product of configurations
- *     (Sec. 2.3.2) and a learned tuner (the data-driven tuning of Sec. 6);
- *   - velocity-Verlet time integration (Sec. 2.1).
+ *     (Sec. 2.3.2), by run time or by energy (Sec. 2.3.3), and a learned tuner
+ *     (the data-driven tuning of Sec. 6) trained by the library's own kernels;
+ *   - velocity-Verlet time integration (Sec. 2.1), for one box or for a batch
+ *     of independent boxes in one persistent launch (lj_ensemble_*).
  *
  * Conventions for every entry point:
  *   - Status codes only: nothing throws, exits or aborts across the ABI.
