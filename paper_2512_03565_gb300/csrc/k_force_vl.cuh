@@ -140,8 +140,11 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
   block_flush<R>(eu_d, ew_d, cnt, out, EV);
 }
 
+// Six blocks of 256 per SM (40 registers) without Newton-3; the atomic
+// variants' extra live values need 48 (five blocks): at 40 they spilled 60-108
+// bytes and ran 9-11 % slower (1,048,576-particle fluid).
 template <typename R, int W, int N3, bool EV, bool I16>
-__global__ void __launch_bounds__(256, 6) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
+__global__ void __launch_bounds__(256, N3 == 1 ? 5 : 6) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
   constexpr int G = 32 / W;
   // Two-lane groups read their list entries in pairs: lane sub takes
   // entries 2 sub and 2 sub + 1 of every 4-entry chunk with one 8-byte load,
