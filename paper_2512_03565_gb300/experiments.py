@@ -40,7 +40,8 @@
 
 * ``force-launch``: a few force evaluations of one configuration on the
   homogeneous fluid (density 0.75, r_c 2.5, skin 0.3) after a warm-up one,
-  for kernel profilers; ``mlp-launch``: one forward and one gradient pass of
+  for kernel profilers (FP32 pair arithmetic unless ``--fp64``; energy and
+  virial with ``--energy``); ``mlp-launch``: one forward and one gradient pass of
   the tuner network on a batch of rows; ``aux-launch``: the auxiliary kernels
   (features, pair lister, 16-bit list copy, getters, quantisation, the
   allocation-free binning, tuner training inputs, a few training epochs) once
@@ -402,6 +403,8 @@ def main(argv=None):
     ap.add_argument("--cfg", default="1,3,4,0", help="force-launch: container,order,param,newton3")
     ap.add_argument("--particles", type=int, default=524288)
     ap.add_argument("--evals", type=int, default=3)
+    ap.add_argument("--fp64", action="store_true", help="force-launch: FP64 pair arithmetic")
+    ap.add_argument("--energy", action="store_true", help="force-launch: also reduce energy and virial")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--data", default="tuner_data.npz")
     ap.add_argument("--model", default=tuner.MODEL_PATH)
@@ -456,15 +459,16 @@ def main(argv=None):
     elif a.what == "force-launch":
         s = W.homogeneous(a.particles, 0.75, W.BASE_SEED + 1, T=1.0, rc=2.5, skin=0.3)
         cfg = lj.config(*[int(v) for v in a.cfg.split(",")])
-        d = lj.Domain(s.L, s.rc, s.skin)
+        prec = lj.LJ_PREC_FP64 if a.fp64 else lj.LJ_PREC_FP32_ACC64
+        d = lj.Domain(s.L, s.rc, s.skin, precision=prec)
         d.set_particles(s.pos, s.vel)
-        d.compute_forces(cfg)
+        d.compute_forces(cfg, a.energy)
         d.timing(1)
         for _ in range(a.evals):
-            d.compute_forces(cfg)
+            d.compute_forces(cfg, a.energy)
         ms, k, _ = d.timing(0)
-        print(json.dumps({"config": lj.config_name(cfg), "n": s.n, "evals": a.evals,
-                          "force_kernel_ms": ms / max(k, 1)}))
+        print(json.dumps({"config": lj.config_name(cfg), "n": s.n, "evals": a.evals, "fp64": a.fp64,
+                          "energy": a.energy, "force_kernel_ms": ms / max(k, 1)}))
         d.close()
     elif a.what == "aux-launch":
         # the library's auxiliary kernels, each launched at least once on a
