@@ -484,7 +484,7 @@ lj_status run_force(Ctx& c, const lj_config& cfg, bool ev, bool acc_zeroed = fal
   CK(e);
   c.launches += force_launches(c, cfg, c.tiles_gen != tiles_before || c.tiles_T != tiles_T_before);
   if (cfg.newton3 == LJ_N3_ATOMIC || cfg.newton3 == LJ_N3_ATOMIC_BWD) {  // unscaled atomic sums
-    CK(launch_scale_check(c));
+    CK(f64 ? launch_scale_check(c) : launch_fold_scale(c));
     c.launches += 1;
   } else if (!(cfg.container == LJ_VL && cfg.newton3 == LJ_N3_OFF)) {  // fused into the VL N3-off store
     CK(launch_check_finite(c));
@@ -1158,7 +1158,7 @@ void lj_destroy(lj_ctx* h) {
                  c.key, c.scan_tmp, c.tiles, c.row_tiles, c.nbr, c.nnbr, c.x_build, c.maxlen, c.twopass,
                  c.rev_cnt, c.rev_start, c.rev_slot, c.rev_key, c.rev_key2, c.ev, c.status,
                  c.feat_stats, c.tile_ctr, c.stage, c.nbr16, c.tower_cl, c.cl_start, c.cl_lo, c.cl_hi, c.cl_z,
-                 c.vcl_nbr, c.vcl_mask, c.vcl_nn};
+                 c.vcl_nbr, c.vcl_mask, c.vcl_nn, c.jacc};
   for (void* p : dev) dfree(p);
   if (c.host_ev) cudaFreeHost(c.host_ev);
   if (c.host_np) cudaFreeHost(c.host_np);

@@ -82,7 +82,7 @@ cudaError_t force_lc_t(Ctx& c, const lj_config& cfg, bool ev) {
   const bool bwd = cfg.newton3 == LJ_N3_ATOMIC_BWD;
   const bool n3 = cfg.newton3 == LJ_N3_ATOMIC || bwd;
   if (n3) {
-    cudaError_t e = cudaMemsetAsync(c.frc, 0, 3 * (size_t)c.n * sizeof(double), c.stream);
+    cudaError_t e = n3_begin(c, out, sizeof(R) == 4);
     if (e != cudaSuccess) return e;
   }
   if (bwd) return ev ? lc_launch<R, true, true, true>(c, cfg, out) : lc_launch<R, true, false, true>(c, cfg, out);
@@ -144,7 +144,7 @@ cudaError_t force_vl_t(Ctx& c, const lj_config& cfg, bool ev) {
   ForceOut out{c.frc, c.frc + c.n, c.frc + 2 * c.n, c.ev, c.npairs, c.status};
   cudaError_t e;
   if (cfg.newton3 == LJ_N3_ATOMIC) {
-    if ((e = cudaMemsetAsync(c.frc, 0, 3 * (size_t)c.n * sizeof(double), c.stream)) != cudaSuccess) return e;
+    if ((e = n3_begin(c, out, sizeof(R) == 4)) != cudaSuccess) return e;
     return ev ? vl_launch<R, 1, true>(c, cfg, out) : vl_launch<R, 1, false>(c, cfg, out);
   }
   if (cfg.newton3 == LJ_N3_TWOPASS) {

@@ -199,10 +199,10 @@ __device__ __forceinline__ bool seg_ok(int kind, uint32_t j, uint32_t i, uint32_
 }
 
 // Add v (R, exactly converted) to an FP64 array element with an atomic.
-// Newton-3 evaluations accumulate the unscaled sums this way (+ for a j, - for
-// an i) and the factor 24 eps / u is applied once per particle afterwards
-// (launch_scale_check): one FP64 multiply per contribution would otherwise run
-// on GB300's narrow FP64 pipe.
+// Newton-3 evaluations accumulate each i's unscaled sum this way (the j side
+// goes through n3_add) and the factor 24 eps / u is applied once per particle
+// afterwards: one FP64 multiply per contribution would otherwise run on
+// GB300's narrow FP64 pipe.
 template <typename R>
 __device__ __forceinline__ void atomic_add_raw(double* p, R v) {
   if (v != (R)0) atomicAdd(p, Prec<R>::to_d(v));
@@ -298,9 +298,7 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
           }
         }
         if (N3 && lane < (int)m) {
-          atomic_add_raw(out.fx + jb + lane, gx);
-          atomic_add_raw(out.fy + jb + lane, gy);
-          atomic_add_raw(out.fz + jb + lane, gz);
+          n3_add<R>(out, jb + lane, gx, gy, gz);
         }
         __syncwarp();
       }
@@ -475,9 +473,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
           if ((q & 31u) == 31u || q + 1 == m) {
             const uint32_t qb = q & ~31u;
             if (lane <= (int)(q - qb)) {
-              atomic_add_raw(out.fx + jb + qb + lane, gx);
-              atomic_add_raw(out.fy + jb + qb + lane, gy);
-              atomic_add_raw(out.fz + jb + qb + lane, gz);
+              n3_add<R>(out, jb + qb + lane, gx, gy, gz);
             }
             gx = gy = gz = 0;
           }
@@ -569,9 +565,7 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
           }
         }
         if (N3 && lane < (int)m) {
-          atomic_add_raw(out.fx + jb + lane, gx);
-          atomic_add_raw(out.fy + jb + lane, gy);
-          atomic_add_raw(out.fz + jb + lane, gz);
+          n3_add<R>(out, jb + lane, gx, gy, gz);
         }
       }
     }
@@ -649,9 +643,7 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
           fy += fac * bf;
           fz += fac * cf_;
           if (N3) {
-            atomic_add_raw(out.fx + j, fac * af);
-            atomic_add_raw(out.fy + j, fac * bf);
-            atomic_add_raw(out.fz + j, fac * cf_);
+            n3_add<R>(out, j, fac * af, fac * bf, fac * cf_);
           }
         }
       }
@@ -675,9 +667,7 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
           fy += fac * bf;
           fz += fac * cf_;
           if (N3) {
-            atomic_add_raw(out.fx + j, fac * af);
-            atomic_add_raw(out.fy + j, fac * bf);
-            atomic_add_raw(out.fz + j, fac * cf_);
+            n3_add<R>(out, j, fac * af, fac * bf, fac * cf_);
           }
         }
       }

@@ -43,8 +43,8 @@ struct VclArgs {
 };
 
 // Without Newton-3 a particle's force is stored once, scaled by -24 eps / u.
-// With it, the unscaled sums are added by atomics (+ for a j, - for an i) and
-// scaled once per particle afterwards (launch_scale_check).
+// With it, the unscaled sums are added (+ for a j through n3_add, - for an i
+// by FP64 atomics) and scaled once per particle afterwards.
 template <typename R>
 __device__ __forceinline__ void store_force(const ForceOut& out, uint32_t i, R fx, R fy, R fz, double s) {
   out.fx[i] = s * Prec<R>::to_d(fx);
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_vcl_tile(LJParams P, VclArgs A, ForceOu
             hz += tz;
           }
         }
-        if (ii == 0 && vj) add_force<R>(out, j, hx, hy, hz);
+        if (ii == 0 && vj) n3_add<R>(out, j, hx, hy, hz);
       }
     }
     // the i force: sum over the j-slots
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_vcl_jlane(LJParams P, VclArgs A, ForceO
           gz += fac * cf;
         }
       }
-      if (N3 && vj) add_force<R>(out, j, gx, gy, gz);
+      if (N3 && vj) n3_add<R>(out, j, gx, gy, gz);
     }
 #pragma unroll
     for (int k = 0; k < M; ++k) {
@@ -246,7 +246,7 @@ template <typename R>
 cudaError_t force_vcl_t(Ctx& c, const lj_config& cfg, bool ev) {
   ForceOut out{c.frc, c.frc + c.n, c.frc + 2 * c.n, c.ev, c.npairs, c.status};
   if (cfg.newton3 == LJ_N3_ATOMIC) {
-    cudaError_t e = cudaMemsetAsync(c.frc, 0, 3 * (size_t)c.n * sizeof(double), c.stream);
+    cudaError_t e = n3_begin(c, out, sizeof(R) == 4);
     if (e != cudaSuccess) return e;
     return ev ? vcl_launch<R, true, true>(c, cfg, out) : vcl_launch<R, true, false>(c, cfg, out);
   }

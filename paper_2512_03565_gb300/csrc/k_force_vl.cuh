@@ -56,8 +56,8 @@ __device__ __forceinline__ void vl_store(const ForceOut& out, uint32_t* status, 
   if (bad) atomicOr(status, ST_NONFINITE);
 }
 
-// Newton-3: the unscaled sum is added (the factor 24 eps / u follows once per
-// particle, launch_scale_check)
+// Newton-3, the i side: the unscaled sum is added to the FP64 force (the
+// factor 24 eps / u follows once per particle); the j side goes through n3_add
 template <typename R>
 __device__ __forceinline__ void vl_atomic(double* p, R v) {
   if (v != (R)0) atomicAdd(p, Prec<R>::to_d(v));
@@ -106,9 +106,7 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
           fy += fac * bf;
           fz += fac * cf;
           if (N3 == 1) {
-            vl_atomic(out.fx + jc[t], fac * af);
-            vl_atomic(out.fy + jc[t], fac * bf);
-            vl_atomic(out.fz + jc[t], fac * cf);
+            n3_add<R>(out, jc[t], fac * af, fac * bf, fac * cf);
           } else if (N3 == 2) {
             if (k0 + t < m) {
               const int64_t e = (int64_t)(k0 + t) * n + i;
@@ -140,11 +138,12 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
   block_flush<R>(eu_d, ew_d, cnt, out, EV);
 }
 
-// Six blocks of 256 per SM (40 registers) without Newton-3; the atomic
-// variants' extra live values need 48 (five blocks): at 40 they spilled 60-108
-// bytes and ran 9-11 % slower (1,048,576-particle fluid).
+// Six blocks of 256 per SM (40 registers) without Newton-3.  The Newton-3
+// variants hold more live values (the j-side contributions and their vector
+// reductions) and get four blocks (64 registers): at five (48) they spilled
+// 8-40 bytes and JSPLIT-2/4 ran 11 % / 8 % slower (1,048,576-particle fluid).
 template <typename R, int W, int N3, bool EV, bool I16>
-__global__ void __launch_bounds__(256, N3 == 1 ? 5 : 6) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
+__global__ void __launch_bounds__(256, N3 == 1 ? 4 : 6) k_vl_jsplit(LJParams P, VLArgs A, ForceOut out) {
   constexpr int G = 32 / W;
   // Two-lane groups read their list entries in pairs: lane sub takes
   // entries 2 sub and 2 sub + 1 of every 4-entry chunk with one 8-byte load,
@@ -216,9 +215,7 @@ __global__ void __launch_bounds__(256, N3 == 1 ? 5 : 6) k_vl_jsplit(LJParams P, 
           fy += fac * bf;
           fz += fac * cf;
           if (N3 == 1) {
-            vl_atomic(out.fx + jc[t], fac * af);
-            vl_atomic(out.fy + jc[t], fac * bf);
-            vl_atomic(out.fz + jc[t], fac * cf);
+            n3_add<R>(out, jc[t], fac * af, fac * bf, fac * cf);
           }
         }
 #pragma unroll

@@ -225,6 +225,45 @@ __global__ void k_scale_check(double* __restrict__ f, int64_t m, double scale, u
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
+// f = scale * (f + the FP32 j-side partial sums), then the finiteness check:
+// the fold of an FP32 Newton-3 evaluation (the i-side sums are already in f).
+__global__ void k_fold_scale(double* __restrict__ f, const float4* __restrict__ jacc, int64_t n, double scale,
+                             uint32_t* __restrict__ status) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = jacc[i];
+    const double v0 = (f[i] + (double)a.x) * scale, v1 = (f[n + i] + (double)a.y) * scale,
+                 v2 = (f[2 * n + i] + (double)a.z) * scale;
+    f[i] = v0;
+    f[n + i] = v1;
+    f[2 * n + i] = v2;
+    bad |= !isfinite(v0) || !isfinite(v1) || !isfinite(v2);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+cudaError_t launch_fold_scale(Ctx& c) {
+  k_fold_scale<<<std::min<unsigned>(nb(c.n, 256), 1024), 256, 0, c.stream>>>(c.frc, (const float4*)c.jacc, c.n,
+                                                                             c.P.e24u, c.status);
+  return cudaGetLastError();
+}
+
+// Start of a Newton-3 evaluation: forces zeroed, and for FP32 pair arithmetic
+// the j-side partial sums too (grown to n particles when needed), named in out.
+cudaError_t n3_begin(Ctx& c, ForceOut& out, bool fp32) {
+  cudaError_t e = cudaMemsetAsync(c.frc, 0, 3 * (size_t)c.n * sizeof(double), c.stream);
+  if (e != cudaSuccess || !fp32) return e;
+  if (c.jacc_cap < (size_t)c.n) {
+    if (c.jacc) cudaFree(c.jacc);
+    c.jacc = nullptr;
+    c.jacc_cap = 0;
+    if ((e = cudaMalloc(&c.jacc, 4 * sizeof(float) * (size_t)c.n)) != cudaSuccess) return e;
+    c.jacc_cap = (size_t)c.n;
+  }
+  out.jacc = c.jacc;
+  return cudaMemsetAsync(c.jacc, 0, 4 * sizeof(float) * (size_t)c.n, c.stream);
+}
+
 cudaError_t launch_scale_check(Ctx& c) {
   k_scale_check<<<std::min<unsigned>(nb(3 * c.n, 256), 1024), 256, 0, c.stream>>>(c.frc, 3 * c.n, c.P.e24u,
                                                                                    c.status);

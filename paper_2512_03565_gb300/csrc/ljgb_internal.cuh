@@ -248,7 +248,32 @@ struct ForceOut {
   double* ev;             // [0] = sum s6(s6-1), [1] = sum s6(2s6-1) (each pair counted per side visited)
   unsigned long long* npairs;  // pair evaluations counted (per side visited)
   uint32_t* status;
+  float* jacc;  // FP32 Newton-3 evaluations: [n][4] j-side partial sums (x, y, z, unused), else null
 };
+
+// One 16-byte vector reduction of (a, b, c, 0) into the float4 at p (16-byte
+// aligned), performed in L2.
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(0.0f)
+               : "memory");
+}
+
+// A Newton-3 contribution to particle k, unscaled (the factor 24 eps / u is
+// applied once per particle afterwards).  FP32 evaluations add it to k's FP32
+// partial sum with one vector reduction (folded into the FP64 force once per
+// particle by launch_fold_scale); FP64 evaluations add it to the FP64 force
+// with three atomics.
+template <typename R>
+__device__ __forceinline__ void n3_add(const ForceOut& out, int64_t k, R x, R y, R z) {
+  if constexpr (sizeof(R) == 4) {
+    if (x != 0.0f || y != 0.0f || z != 0.0f) red_add_v4(out.jacc + 4 * k, x, y, z);
+  } else {
+    if (x != 0.0) atomicAdd(out.fx + k, x);
+    if (y != 0.0) atomicAdd(out.fy + k, y);
+    if (z != 0.0) atomicAdd(out.fz + k, z);
+  }
+}
 
 // Block-level reduction of the energy/virial partials and pair counts; one
 // atomic per block.  Every thread of the block must call it.
@@ -325,6 +350,8 @@ struct Ctx {
   double* vel_alt = nullptr;
   double* frc = nullptr;   // [3][n] forces of the last evaluation
   double* frc_alt = nullptr;
+  float* jacc = nullptr;    // [n][4] FP32 Newton-3 partial sums of the j side
+  size_t jacc_cap = 0;      // particles it holds
   bool forces_valid = false;
   // closing half kick of the last integrated step, not yet applied: velocities
   // are at the half step and v += kick_hdtm * F is due (see lj_integrate_step)
@@ -503,6 +530,8 @@ cudaError_t launch_feature_stats(Ctx& c, unsigned long long* stats);
 cudaError_t launch_ke(Ctx& c, double* out);
 cudaError_t launch_check_finite(Ctx& c);
 cudaError_t launch_scale_check(Ctx& c);
+cudaError_t launch_fold_scale(Ctx& c);
+cudaError_t n3_begin(Ctx& c, ForceOut& out, bool fp32);
 cudaError_t launch_lc_pairs(Ctx& c, unsigned long long* count, int2* out, size_t cap);
 
 }  // namespace ljgb

@@ -283,19 +283,22 @@ def traversal(n=500_000, samples=5, log=print):
     return out
 
 
-def c2_sweep(steps=100, skip=10, repeats=5, dt=0.002, log=print):
+def c2_sweep(steps=100, skip=10, repeats=5, dt=0.002, only=None, log=print):
     """The 1,048,576-particle fluid (density 0.75, skin 0.3, lists rebuilt every
     10 steps) run with every valid configuration: `repeats` fresh MD runs of
     `steps` velocity-Verlet steps from the same start; per run the mean
     force-kernel time over steps skip..steps (CUDA events around each force
     launch), per configuration the minimum over the runs, with the whole-step
     wall time (host-synchronised) and the unique in-cutoff pairs of the last
-    evaluation.  Caches are not flushed between steps."""
+    evaluation.  Caches are not flushed between steps.  `only`: run just the
+    configurations whose name contains one of these substrings."""
     import torch
     s = W.config2()
     out = {}
     for cfg in lj.configs():
         name = lj.config_name(cfg)
+        if only and not any(o in name for o in only):
+            continue
         force, step, pairs = [], [], 0
         for _ in range(repeats):
             d = lj.Domain(s.L, s.rc, s.skin, precision=lj.LJ_PREC_FP32_ACC64)
@@ -403,6 +406,7 @@ def main(argv=None):
     ap.add_argument("--cfg", default="1,3,4,0", help="force-launch: container,order,param,newton3")
     ap.add_argument("--particles", type=int, default=524288)
     ap.add_argument("--evals", type=int, default=3)
+    ap.add_argument("--only", default=None, help="c2-sweep: comma-separated name substrings to run")
     ap.add_argument("--fp64", action="store_true", help="force-launch: FP64 pair arithmetic")
     ap.add_argument("--energy", action="store_true", help="force-launch: also reduce energy and virial")
     ap.add_argument("--scale", type=float, default=1.0)
@@ -519,7 +523,7 @@ def main(argv=None):
         lj.mlp_loss_grad(model["params"], C_out, X, T, M)
         print(json.dumps({"rows": 4096, "outputs": C_out}))
     elif a.what == "c2-sweep":
-        res = c2_sweep()
+        res = c2_sweep(only=a.only.split(",") if a.only else None)
         if a.out:
             json.dump(res, open(a.out, "w"))
     elif a.what == "clusters":
