@@ -209,7 +209,7 @@ __global__ void k_check_finite(const double* __restrict__ f, int64_t m, uint32_t
 }
 
 cudaError_t launch_check_finite(Ctx& c) {
-  k_check_finite<<<std::min<unsigned>(nb(3 * c.n, 256), 1024), 256, 0, c.stream>>>(c.frc, 3 * c.n, c.status);
+  k_check_finite<<<nb(3 * c.n, 256), 256, 0, c.stream>>>(c.frc, 3 * c.n, c.status);
   return cudaGetLastError();
 }
 
@@ -243,8 +243,7 @@ __global__ void k_fold_scale(double* __restrict__ f, const float4* __restrict__ 
 }
 
 cudaError_t launch_fold_scale(Ctx& c) {
-  k_fold_scale<<<std::min<unsigned>(nb(c.n, 256), 1024), 256, 0, c.stream>>>(c.frc, (const float4*)c.jacc, c.n,
-                                                                             c.P.e24u, c.status);
+  k_fold_scale<<<nb(c.n, 256), 256, 0, c.stream>>>(c.frc, (const float4*)c.jacc, c.n, c.P.e24u, c.status);
   return cudaGetLastError();
 }
 
@@ -265,8 +264,7 @@ cudaError_t n3_begin(Ctx& c, ForceOut& out, bool fp32) {
 }
 
 cudaError_t launch_scale_check(Ctx& c) {
-  k_scale_check<<<std::min<unsigned>(nb(3 * c.n, 256), 1024), 256, 0, c.stream>>>(c.frc, 3 * c.n, c.P.e24u,
-                                                                                   c.status);
+  k_scale_check<<<nb(3 * c.n, 256), 256, 0, c.stream>>>(c.frc, 3 * c.n, c.P.e24u, c.status);
   return cudaGetLastError();
 }
 
