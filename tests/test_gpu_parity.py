@@ -110,6 +110,36 @@ def test_dilute_gas_with_close_contacts(lj):
             assert worst <= tol, (seed, prec, name, worst)
 
 
+def test_newton3_partial_sums_across_particle_counts(lj):
+    """FP32 Newton-3 evaluations add each j contribution to j's FP32 partial
+    sum in a per-domain buffer, which grows with the particle count and is
+    cleared before every evaluation.  One domain takes 2,500 particles, then
+    4,000 (the buffer grows), then the 2,500 again (a larger buffer than
+    needed); every Newton-3 configuration is evaluated twice on each, and
+    every evaluation must match the oracle within the FP32 bound with exact
+    pair counts (a buffer left uncleared would double the j sides)."""
+    a = W.stratified(2500, 0.6, 311)
+    b = W.stratified(4000, 0.96, 312)  # the same box edge: 2500 / 0.6 = 4000 / 0.96
+    assert abs(a.L - b.L) < 1e-9 * a.L
+    refs = [oracle.forces_bruteforce(s.pos, a.L, a.rc) for s in (a, b)]
+    n3 = [c for c in lj.configs() if c.newton3 in (lj.LJ_N3_ATOMIC, lj.LJ_N3_ATOMIC_BWD)]
+    assert len(n3) > 20
+    d = lj.Domain(a.L, a.rc, a.skin, precision=lj.LJ_PREC_FP32_ACC64)
+    bad = []
+    for k in (0, 1, 0):
+        s = (a, b)[k]
+        F_ref, _, _, np_ref = refs[k]
+        d.set_particles(s.pos, s.vel)
+        for cfg in n3:
+            for _ in range(2):
+                d.compute_forces(cfg)
+                e = rel_err(d.forces(), F_ref)
+                if not (e <= TOL[1] and d.counters()[1] == np_ref):
+                    bad.append((s.n, lj.config_name(cfg), e, d.counters()[1], np_ref))
+    d.close()
+    assert not bad, bad[:5]
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_config1_uniform_1000(lj, prec):
     """1,000 particles, uniform random at density 0.8, rc 2.5, one evaluation."""
