@@ -109,9 +109,14 @@ typedef enum {
 } lj_order;
 
 /* Newton's third law (Sec. 2.1, Sec. 4.1.3): off (every pair evaluated from
- * both sides), on with the j contribution scattered by FP64 atomics, or on with
- * a deterministic two-pass reduction (j partials written to a buffer, then
- * gathered per particle in a fixed order; Verlet lists, VL_IPT only).
+ * both sides), on with the j contribution scattered by atomics, or on with a
+ * deterministic two-pass reduction (j partials written to a buffer, then
+ * gathered per particle in a fixed order; Verlet lists, VL_IPT only).  With
+ * FP32 pair arithmetic the atomic scatter is one 16-byte FP32 vector
+ * reduction per contribution into the particle's FP32 partial sum (performed
+ * in L2; its order of summation, and so the last bits of the result, vary
+ * between runs), folded once per particle into the FP64 force; with FP64 pair
+ * arithmetic it is FP64 atomics on the force itself.
  * LJ_N3_ATOMIC_BWD (linked cells only) is LJ_N3_ATOMIC with the roles of the
  * two cells of every cell pair swapped: each i visits the backward half shell
  * (the neighbour cells before its own in cell order) instead of the forward
