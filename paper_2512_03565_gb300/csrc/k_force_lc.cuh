@@ -198,16 +198,6 @@ __device__ __forceinline__ bool seg_ok(int kind, uint32_t j, uint32_t i, uint32_
   return kind == 1 ? (j > i) : (cxi == (uint32_t)(nc - 1));
 }
 
-// Add v (R, exactly converted) to an FP64 array element with an atomic.
-// Newton-3 evaluations accumulate each i's unscaled sum this way (the j side
-// goes through n3_add) and the factor 24 eps / u is applied once per particle
-// afterwards: one FP64 multiply per contribution would otherwise run on
-// GB300's narrow FP64 pipe.
-template <typename R>
-__device__ __forceinline__ void atomic_add_raw(double* p, R v) {
-  if (v != (R)0) atomicAdd(p, Prec<R>::to_d(v));
-}
-
 struct LCArgs {
   const uint4* pos;
   const uint32_t* cs;
@@ -307,9 +297,7 @@ __global__ void __launch_bounds__(256) k_lc_ipt(LJParams P, LCArgs A, ForceOut o
     for (int k = 0; k < K; ++k) {
       if (!vi[k]) continue;
       if (N3) {
-        atomic_add_raw(out.fx + ii[k], -fx[k]);
-        atomic_add_raw(out.fy + ii[k], -fy[k]);
-        atomic_add_raw(out.fz + ii[k], -fz[k]);
+        n3_add<R>(out, ii[k], -fx[k], -fy[k], -fz[k]);
       } else {
         out.fx[ii[k]] = -P.e24u * Prec<R>::to_d(fx[k]);
         out.fy[ii[k]] = -P.e24u * Prec<R>::to_d(fy[k]);
@@ -487,9 +475,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32) k_lc_tma(LJParams P, LCArgs A,
     if (failed) break;
     if (vi) {
       if (N3) {
-        atomic_add_raw(out.fx + ii, -fx);
-        atomic_add_raw(out.fy + ii, -fy);
-        atomic_add_raw(out.fz + ii, -fz);
+        n3_add<R>(out, ii, -fx, -fy, -fz);
       } else {
         out.fx[ii] = -P.e24u * Prec<R>::to_d(fx);
         out.fy[ii] = -P.e24u * Prec<R>::to_d(fy);
@@ -571,9 +557,7 @@ __global__ void __launch_bounds__(256) k_lc_rot(LJParams P, LCArgs A, ForceOut o
     }
     if (vi) {
       if (N3) {
-        atomic_add_raw(out.fx + ii, -fx);
-        atomic_add_raw(out.fy + ii, -fy);
-        atomic_add_raw(out.fz + ii, -fz);
+        n3_add<R>(out, ii, -fx, -fy, -fz);
       } else {
         out.fx[ii] = -P.e24u * Prec<R>::to_d(fx);
         out.fy[ii] = -P.e24u * Prec<R>::to_d(fy);
@@ -680,9 +664,7 @@ __global__ void __launch_bounds__(256) k_lc_jsplit(LJParams P, const uint4* __re
     }
     if (vi && sub == 0) {
       if (N3) {
-        atomic_add_raw(out.fx + ii, -fx);
-        atomic_add_raw(out.fy + ii, -fy);
-        atomic_add_raw(out.fz + ii, -fz);
+        n3_add<R>(out, ii, -fx, -fy, -fz);
       } else {
         out.fx[ii] = -P.e24u * Prec<R>::to_d(fx);
         out.fy[ii] = -P.e24u * Prec<R>::to_d(fy);

@@ -43,20 +43,13 @@ struct VclArgs {
 };
 
 // Without Newton-3 a particle's force is stored once, scaled by -24 eps / u.
-// With it, the unscaled sums are added (+ for a j through n3_add, - for an i
-// by FP64 atomics) and scaled once per particle afterwards.
+// With it, the unscaled sums are added through n3_add (+ for a j, - for an
+// i) and scaled once per particle afterwards.
 template <typename R>
 __device__ __forceinline__ void store_force(const ForceOut& out, uint32_t i, R fx, R fy, R fz, double s) {
   out.fx[i] = s * Prec<R>::to_d(fx);
   out.fy[i] = s * Prec<R>::to_d(fy);
   out.fz[i] = s * Prec<R>::to_d(fz);
-}
-
-template <typename R>
-__device__ __forceinline__ void add_force(const ForceOut& out, uint32_t i, R fx, R fy, R fz) {
-  if (fx != (R)0) atomicAdd(out.fx + i, Prec<R>::to_d(fx));
-  if (fy != (R)0) atomicAdd(out.fy + i, Prec<R>::to_d(fy));
-  if (fz != (R)0) atomicAdd(out.fz + i, Prec<R>::to_d(fz));
 }
 
 template <typename R, int M, bool N3, bool EV>
@@ -134,7 +127,7 @@ __global__ void __launch_bounds__(256) k_vcl_tile(LJParams P, VclArgs A, ForceOu
       fz = sz;
     }
     if (vi && js == 0) {
-      if (N3) add_force<R>(out, i, -fx, -fy, -fz);
+      if (N3) n3_add<R>(out, i, -fx, -fy, -fz);
       else store_force<R>(out, i, fx, fy, fz, -P.e24u);
     }
     if (EV) {
@@ -205,7 +198,7 @@ __global__ void __launch_bounds__(256) k_vcl_jlane(LJParams P, VclArgs A, ForceO
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
       }
       if (lane == 0 && (uint32_t)k < ni) {
-        if (N3) add_force<R>(out, ib + k, -sx, -sy, -sz);
+        if (N3) n3_add<R>(out, ib + k, -sx, -sy, -sz);
         else store_force<R>(out, ib + k, sx, sy, sz, -P.e24u);
       }
     }

@@ -56,13 +56,6 @@ __device__ __forceinline__ void vl_store(const ForceOut& out, uint32_t* status, 
   if (bad) atomicOr(status, ST_NONFINITE);
 }
 
-// Newton-3, the i side: the unscaled sum is added to the FP64 force (the
-// factor 24 eps / u follows once per particle); the j side goes through n3_add
-template <typename R>
-__device__ __forceinline__ void vl_atomic(double* p, R v) {
-  if (v != (R)0) atomicAdd(p, Prec<R>::to_d(v));
-}
-
 // Entries are processed in batches of VL_BATCH: the batch's list entries are
 // loaded, then its positions gathered, then its pairs computed, so that every
 // lane keeps several independent gathers in flight.  A short last batch is
@@ -122,9 +115,7 @@ __global__ void __launch_bounds__(256) k_vl_ipt(LJParams P, VLArgs A, ForceOut o
         for (int t = 0; t < VL_BATCH; ++t) jc[t] = jn[t];
       }
       if (N3 == 1) {
-        vl_atomic(out.fx + i, -fx);
-        vl_atomic(out.fy + i, -fy);
-        vl_atomic(out.fz + i, -fz);
+        n3_add<R>(out, i, -fx, -fy, -fz);
       } else {
         vl_store(out, A.status, i, -P.e24u * Prec<R>::to_d(fx), -P.e24u * Prec<R>::to_d(fy),
                  -P.e24u * Prec<R>::to_d(fz));
@@ -230,9 +221,7 @@ __global__ void __launch_bounds__(256, N3 == 1 ? 4 : 6) k_vl_jsplit(LJParams P, 
     }
     if (vi && sub == 0) {
       if (N3 == 1) {
-        vl_atomic(out.fx + i, -fx);
-        vl_atomic(out.fy + i, -fy);
-        vl_atomic(out.fz + i, -fz);
+        n3_add<R>(out, i, -fx, -fy, -fz);
       } else {
         vl_store(out, A.status, i, -P.e24u * Prec<R>::to_d(fx), -P.e24u * Prec<R>::to_d(fy),
                  -P.e24u * Prec<R>::to_d(fz));

@@ -225,15 +225,15 @@ __global__ void k_scale_check(double* __restrict__ f, int64_t m, double scale, u
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
-// f = scale * (f + the FP32 j-side partial sums), then the finiteness check:
-// the fold of an FP32 Newton-3 evaluation (the i-side sums are already in f).
+// f = scale * the FP32 partial sums, then the finiteness check: the fold of
+// an FP32 Newton-3 evaluation, whose kernels add both sides of every pair to
+// the partial sums.
 __global__ void k_fold_scale(double* __restrict__ f, const float4* __restrict__ jacc, int64_t n, double scale,
                              uint32_t* __restrict__ status) {
   bool bad = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 a = jacc[i];
-    const double v0 = (f[i] + (double)a.x) * scale, v1 = (f[n + i] + (double)a.y) * scale,
-                 v2 = (f[2 * n + i] + (double)a.z) * scale;
+    const double v0 = (double)a.x * scale, v1 = (double)a.y * scale, v2 = (double)a.z * scale;
     f[i] = v0;
     f[n + i] = v1;
     f[2 * n + i] = v2;
@@ -247,11 +247,12 @@ cudaError_t launch_fold_scale(Ctx& c) {
   return cudaGetLastError();
 }
 
-// Start of a Newton-3 evaluation: forces zeroed, and for FP32 pair arithmetic
-// the j-side partial sums too (grown to n particles when needed), named in out.
+// Start of a Newton-3 evaluation: the sums it accumulates into are zeroed,
+// the FP64 forces for FP64 pair arithmetic, else the FP32 partial sums (grown
+// to n particles when needed, and named in out).
 cudaError_t n3_begin(Ctx& c, ForceOut& out, bool fp32) {
-  cudaError_t e = cudaMemsetAsync(c.frc, 0, 3 * (size_t)c.n * sizeof(double), c.stream);
-  if (e != cudaSuccess || !fp32) return e;
+  cudaError_t e;
+  if (!fp32) return cudaMemsetAsync(c.frc, 0, 3 * (size_t)c.n * sizeof(double), c.stream);
   if (c.jacc_cap < (size_t)c.n) {
     if (c.jacc) cudaFree(c.jacc);
     c.jacc = nullptr;

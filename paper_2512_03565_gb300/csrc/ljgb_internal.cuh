@@ -248,7 +248,7 @@ struct ForceOut {
   double* ev;             // [0] = sum s6(s6-1), [1] = sum s6(2s6-1) (each pair counted per side visited)
   unsigned long long* npairs;  // pair evaluations counted (per side visited)
   uint32_t* status;
-  float* jacc;  // FP32 Newton-3 evaluations: [n][4] j-side partial sums (x, y, z, unused), else null
+  float* jacc;  // FP32 Newton-3 evaluations: [n][4] partial sums (x, y, z, unused), else null
 };
 
 // One 16-byte vector reduction of (a, b, c, 0) into the float4 at p (16-byte
@@ -260,9 +260,10 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c) 
 }
 
 // A Newton-3 contribution to particle k, unscaled (the factor 24 eps / u is
-// applied once per particle afterwards).  FP32 evaluations add it to k's FP32
-// partial sum with one vector reduction (folded into the FP64 force once per
-// particle by launch_fold_scale); FP64 evaluations add it to the FP64 force
+// applied once per particle afterwards): a j's share of one pair, or an i's
+// sum over its pairs.  FP32 evaluations add it to k's FP32 partial sum with
+// one vector reduction (the only record of k's force until launch_fold_scale
+// writes the FP64 force from it); FP64 evaluations add it to the FP64 force
 // with three atomics.
 template <typename R>
 __device__ __forceinline__ void n3_add(const ForceOut& out, int64_t k, R x, R y, R z) {
@@ -350,7 +351,7 @@ struct Ctx {
   double* vel_alt = nullptr;
   double* frc = nullptr;   // [3][n] forces of the last evaluation
   double* frc_alt = nullptr;
-  float* jacc = nullptr;    // [n][4] FP32 Newton-3 partial sums of the j side
+  float* jacc = nullptr;    // [n][4] FP32 Newton-3 partial sums
   size_t jacc_cap = 0;      // particles it holds
   bool forces_valid = false;
   // closing half kick of the last integrated step, not yet applied: velocities
